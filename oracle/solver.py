@@ -300,7 +300,11 @@ def dacg_newton(A, p: int, X0: np.ndarray, opt: OracleOptions, ic=None):
             if Qt.shape[1]:
                 u_new = u_new - Qt @ (Qt.T @ u_new)
                 u_new = u_new / np.linalg.norm(u_new)
-            if opt.k_max > 0:
+            # Theorem 3.2: the update keeps Phat SPD when alpha = s^T r < 0,
+            # which holds when the correction equation is solved; a pair
+            # with alpha >= 0 (e.g. s = 0 after an immediate PCG breakdown)
+            # defines no SPD update and is not stored.
+            if opt.k_max > 0 and s @ r < 0:
                 if len(S) == opt.k_max:
                     S.pop(0)
                     R.pop(0)
