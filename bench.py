@@ -1,0 +1,365 @@
+"""Benchmark: eigenpairs/s of the DACG-Newton solve on the 100^3 variable-
+coefficient diffusion matrix (n = 1e6, 7-point, p = 10, IC(10, 1e-3),
+relative residual 1e-8), with the inner-PCG HBM roofline.
+
+A "step" is one complete nle_solve: DACG + Newton with every inner PCG
+iteration for all p eigenpairs, inputs (factored matrix, start vectors)
+resident on the device.  The IC factorisation is set-up and is reported
+separately (``ic_seconds``), as the paper reports its "IC CPU" column.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp64]
+  python bench.py --impl reference ...    # the oracle on the host cores
+
+Under torchrun (N > 1) every rank solves its own replica of the problem
+(one problem does not shard) and rank 0 prints the line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "diff3d7_100"
+METRIC = "eigenpairs/s at n=1e6, rel. residual 1e-8"
+UNIT = "eigenpairs/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--sample-eigenpairs", type=int, default=1, help=argparse.SUPPRESS)
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# oracle timing (CPU baseline and the reference arm)
+# ---------------------------------------------------------------------------
+
+def cpu_sample(workload: str, npairs: int) -> dict:
+    """Time the oracle, as it stands, on the first `npairs` eigenpairs of the
+    workload (IC set-up excluded).  Runs in this process: the caller starts
+    it as a single-threaded subprocess."""
+    import oracle as O
+    import workloads as W
+
+    A, st = W.workload(workload)
+    ic = O.ic_factor(A, st["lfil"], st["tau_ic"])
+    X0 = W.start_vectors(A.n, npairs, st["seed"])
+    opt = O.OracleOptions(tol=st["tol"], lfil=st["lfil"], tau_ic=st["tau_ic"])
+    t0 = time.perf_counter()
+    lam, V, stats = O.dacg_newton(A, npairs, X0, opt, ic=ic)
+    sec = time.perf_counter() - t0
+    return dict(seconds=sec, eigenpairs=npairs, lam=[float(x) for x in lam])
+
+
+def run_cpu_sample(workload: str, npairs: int) -> dict:
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-sample", "--workload", workload,
+                        "--sample-eigenpairs", str(npairs)], env=env, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError("oracle sample failed: " + r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline_entry(res: dict, workload: str) -> dict:
+    return dict(value=res["eigenpairs"] / res["seconds"], unit=UNIT, cores=1, kind="oracle",
+                sample=f"oracle (numpy + plain C, FP64, 1 thread) on eigenpair 1 of {workload} "
+                       f"({res['eigenpairs']} eigenpair, {res['seconds']:.1f} s, IC set-up excluded)")
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    times = []
+    for i in range(args.warmup + args.steps):
+        res = run_cpu_sample(args.workload, 1)
+        if i >= args.warmup:
+            times.append(res["seconds"])
+    total = sum(times)
+    value = args.steps / total
+    line = dict(impl="reference", metric=METRIC, value=value, unit=UNIT, n_gpus=args.gpus, steps=args.steps,
+                warmup=args.warmup, ms_per_step=1000 * total / args.steps, higher_is_better=True, scaling="weak",
+                vs_baseline=None, dtype="f64", data="synthetic",
+                config=dict(workload=args.workload, sample="eigenpair 1 per step (DACG + Newton), IC set-up excluded"),
+                cpu_baseline=dict(value=value, unit=UNIT, cores=1, kind="oracle",
+                                  sample="eigenpair 1 of the workload per step, 1 thread"),
+                e2e=dict(value=value, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return dict(sm_mhz=None, sm_max_mhz=None, reasons=["nvidia-smi unavailable"])
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    smax.append(float(f[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, f[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        return dict(sm_mhz=statistics.median(sm) if sm else None, sm_max_mhz=max(smax) if smax else None,
+                    reasons=sorted(reasons), samples=len(sm))
+
+
+# ---------------------------------------------------------------------------
+# roofline accounting
+# ---------------------------------------------------------------------------
+
+def alg_bytes(n, nnz_a, nnz_l, w, its, sum_m, sum_k, kind):
+    """Algorithmic HBM bytes of `its` iterations.
+
+    Matrix terms: B_A = nnz_A (w + 4) + 4 (n + 1), B_L = nnz_L (w + 4) + 4 (n + 1)
+    (values + int32 column indices + row pointers).
+    Inner PCG iteration (fused schedule): B_A + 2 B_L + (16 + 4k + 4m) n w.
+    DACG iteration: B_A + 2 B_L + (16 + 2m) n w.
+    """
+    BA = nnz_a * (w + 4) + 4 * (n + 1)
+    BL = nnz_l * (w + 4) + 4 * (n + 1)
+    V = n * w
+    if kind == "pcg":
+        return its * (BA + 2 * BL + 16 * V) + 4 * V * (sum_k + sum_m)
+    return its * (BA + 2 * BL + 16 * V) + 2 * V * sum_m
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_1312_1553_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def load_traffic(kernel: str):
+    """ncu dram bytes per launch of `kernel`, if captured for the current sources."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(p) as fh:
+            t = json.load(fh)
+    except Exception:
+        return None
+    e = t.get(kernel)
+    if not e or e.get("kernel_hash") != kernel_hash():
+        return None
+    return e.get("bytes_per_launch")
+
+
+def peak_hbm():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def main():
+    args = parse()
+    if args.cpu_sample:
+        print(json.dumps(cpu_sample(args.workload, args.sample_eigenpairs)))
+        return 0
+    if args.impl == "reference":
+        return reference_arm(args)
+    if args.warmup < 3:
+        print("warning: --warmup < 3 is below the timing rules", file=sys.stderr)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    # CPU baseline before any GPU work (rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:
+            cpu = cpu_baseline_entry(run_cpu_sample(args.workload, 1), args.workload)
+        except Exception as e:  # reported, not fatal
+            cpu = dict(value=None, unit=UNIT, cores=1, kind="oracle", sample=f"failed: {e}")
+
+    import numpy as np
+    import torch
+
+    import workloads as W
+    from paper_1312_1553_gb300 import _build, nle
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    _build.build()
+    nle.load_library()
+
+    A, st = W.workload(args.workload)
+    p = st["p"]
+    X0 = W.start_vectors(A.n, p, st["seed"])
+    prec = nle.NLE_MIXED if args.precision == "mixed" else nle.NLE_FP64
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        s = nle.Eigensolver(A, dict(precision=prec), stream=stream)
+        t0 = time.perf_counter()
+        s.factor_ic(st["lfil"], st["tau_ic"])
+        ic_seconds = time.perf_counter() - t0
+        F = s.get_factor()
+        nnz_l = int(F["Lrowptr"][-1])
+        x0 = torch.tensor(X0, dtype=torch.float64, device="cuda")
+        lam = torch.empty(p, dtype=torch.float64, device="cuda")
+        V = torch.empty((p, A.n), dtype=torch.float64, device="cuda")
+
+        def step():
+            stats = nle.nle_stats()
+            rc = nle.nle_solve(s.h, p, st["tol"], 100, 20, nle._dptr(x0), nle._dptr(lam), nle._dptr(V), stats, 1)
+            if rc != 0:
+                raise nle.NLEError(rc, nle.nle_last_error(s.h))
+            return nle.stats_dict(stats)
+
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        clk = ClockSampler(local)
+        clk.start()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        all_stats = [step() for _ in range(args.steps)]
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        clocks = clk.stop()
+        ms = ev0.elapsed_time(ev1)
+        # end to end through the C ABI with host buffers (pinned), copies inside
+        x0_h = torch.tensor(X0, dtype=torch.float64).pin_memory()
+        lam_h = torch.empty(p, dtype=torch.float64).pin_memory()
+        V_h = torch.empty((p, A.n), dtype=torch.float64).pin_memory()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            stats = nle.nle_stats()
+            rc = nle.nle_solve(s.h, p, st["tol"], 100, 20, nle._dptr(x0_h), nle._dptr(lam_h), nle._dptr(V_h),
+                               stats, 0)
+            if rc != 0:
+                raise nle.NLEError(rc, nle.nle_last_error(s.h))
+            _ = float(lam_h[0])
+        e2e_sec = time.perf_counter() - t0
+        lam_dev = lam.cpu().numpy()
+        s.close()
+
+    # max over ranks
+    t_max = ms / 1000.0
+    e2e_max = e2e_sec
+    if world > 1:
+        tt = torch.tensor([t_max, e2e_max], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_max, e2e_max = float(tt[0]), float(tt[1])
+    value = world * p * args.steps / t_max
+    e2e_value = world * p * args.steps / e2e_max
+
+    # roofline of the dominant kernel (Newton phase or DACG phase)
+    w = 4 if prec == nle.NLE_MIXED else 8
+    ms_newton = sum(x["ms_newton"] for x in all_stats)
+    ms_dacg = sum(x["ms_dacg"] for x in all_stats)
+    its = sum(x["pcg_iterations"] for x in all_stats)
+    b_newton = alg_bytes(A.n, A.nnz, nnz_l, w, its, sum(x["pcg_sum_m"] for x in all_stats),
+                         sum(x["pcg_sum_k"] for x in all_stats), "pcg")
+    dits = sum(x["dacg_iterations"] for x in all_stats)
+    b_dacg = alg_bytes(A.n, A.nnz, nnz_l, w, dits, sum(x["dacg_sum_m"] for x in all_stats), 0, "dacg")
+    peak, peak_kind = peak_hbm()
+    launches_per_step = p  # one persistent launch of each phase kernel per eigenpair
+    kern = "k_newton" if ms_newton >= ms_dacg else "k_dacg"
+    b, msk = (b_newton, ms_newton) if kern == "k_newton" else (b_dacg, ms_dacg)
+    achieved = (b / 1e9) / (msk / 1e3)
+    nlaunch = launches_per_step * args.steps
+    traffic = load_traffic(kern)
+    roof = dict(bound="hbm", achieved=achieved, peak=peak, unit="GB/s", frac=achieved / peak, traffic=traffic,
+                kernel=kern, peak_source=f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)" if peak_kind == "measured" else
+                "fallback 6.8 TB/s", alg_bytes_per_launch=b / nlaunch, ms_per_launch=msk / nlaunch,
+                other=dict(kernel="k_dacg" if kern == "k_newton" else "k_newton",
+                           achieved=((b_dacg if kern == "k_newton" else b_newton) / 1e9) /
+                           (max(ms_dacg if kern == "k_newton" else ms_newton, 1e-9) / 1e3)))
+    line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
+                ms_per_step=1000 * t_max / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
+                dtype="f32" if prec == nle.NLE_MIXED else "f64", data="synthetic",
+                config=dict(workload=f"{args.workload}: 3D 7-point diffusion 100^3, exp(Gaussian field) faces",
+                            n=A.n, nnz=A.nnz, p=p, lfil=st["lfil"], tau_ic=st["tau_ic"], tol=st["tol"],
+                            precision="FP32 bulk + FP64 outer step" if prec == nle.NLE_MIXED else "FP64",
+                            nnz_L=nnz_l, nlev_L=F["nlevL"], ic_seconds=ic_seconds,
+                            l2="working set > 129 MB L2 (no flush needed)",
+                            parallelism=f"replicas{world}" if world > 1 else "single GPU"),
+                roofline=roof, cpu_baseline=cpu,
+                e2e=dict(value=e2e_value, unit=UNIT, h2d_bytes_per_step=p * A.n * 8,
+                         d2h_bytes_per_step=p * A.n * 8 + p * 8),
+                clocks=clocks, gpu_launches=int(sum(x["kernel_launches"] for x in all_stats)),
+                phase_ms=dict(dacg=ms_dacg / args.steps, newton=ms_newton / args.steps),
+                iterations=dict(pcg=its / args.steps, dacg=dits / args.steps),
+                lambda_first=float(lam_dev[0]))
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

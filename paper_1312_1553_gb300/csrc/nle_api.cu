@@ -1,0 +1,742 @@
+// C ABI of the nle library (include/nle.h): handle management, device
+// memory, cooperative launches of the persistent kernels and the small
+// relabelling kernels around them.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/nle.h"
+#include "nle_device.cuh"
+#include "nle_internal.h"
+#include "nle_setup.h"
+
+namespace nle {
+// one translation unit of nle_kernels.cu per (precision, rows-per-thread)
+void *kernel_ptr_f1(int);
+void *kernel_ptr_f2(int);
+void *kernel_ptr_f4(int);
+void *kernel_ptr_f8(int);
+void *kernel_ptr_d1(int);
+void *kernel_ptr_d2(int);
+void *kernel_ptr_d4(int);
+void *kernel_ptr_d8(int);
+enum KernelId { K_NEWTON = 0, K_DACG = 1, K_SHIFTED = 2, K_PREC = 3, K_PCG = 4 };
+template <typename T>
+void *kernel_ptr(int id, int rpc);
+template <>
+void *kernel_ptr<float>(int id, int rpc) {
+  switch (rpc) {
+    case 1: return kernel_ptr_f1(id);
+    case 2: return kernel_ptr_f2(id);
+    case 4: return kernel_ptr_f4(id);
+    case 8: return kernel_ptr_f8(id);
+  }
+  return nullptr;
+}
+template <>
+void *kernel_ptr<double>(int id, int rpc) {
+  switch (rpc) {
+    case 1: return kernel_ptr_d1(id);
+    case 2: return kernel_ptr_d2(id);
+    case 4: return kernel_ptr_d4(id);
+    case 8: return kernel_ptr_d8(id);
+  }
+  return nullptr;
+}
+
+// ---------------------------------------------------------------------------
+// relabelling kernels
+// ---------------------------------------------------------------------------
+// dst[i] = T(src[perm[i]]) for i < n, 0 for n <= i < npad
+template <typename T>
+__global__ void k_gather(T *dst, const double *src, const int32_t *perm, int64_t n, int64_t npad) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < npad; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = (i < n) ? T(src[perm[i]]) : T(0);
+}
+// dst[o] = double(src[iperm[o]]) for o < n
+template <typename T>
+__global__ void k_scatter(double *dst, const T *src, const int32_t *iperm, int64_t n) {
+  for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < n; o += (int64_t)gridDim.x * blockDim.x)
+    dst[o] = double(src[iperm[o]]);
+}
+// V[j*n + o] = sgn_j * Qt[j*npad + iperm[o]], sgn_j making the entry of
+// largest modulus positive (lowest natural index on ties).  One block per j.
+__global__ void k_output_vectors(double *V, const double *Qt, const int32_t *iperm, int64_t n, int64_t npad) {
+  const int j = blockIdx.x;
+  const double *q = Qt + (int64_t)j * npad;
+  double best = -1.0;
+  int64_t bi = 0;
+  for (int64_t o = threadIdx.x; o < n; o += blockDim.x) {
+    const double a = fabs(q[iperm[o]]);
+    if (a > best) best = a, bi = o;
+  }
+  __shared__ double sb[1024];
+  __shared__ int64_t si[1024];
+  sb[threadIdx.x] = best;
+  si[threadIdx.x] = bi;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      const double b2 = sb[threadIdx.x + s];
+      const int64_t i2 = si[threadIdx.x + s];
+      if (b2 > sb[threadIdx.x] || (b2 == sb[threadIdx.x] && i2 < si[threadIdx.x])) sb[threadIdx.x] = b2, si[threadIdx.x] = i2;
+    }
+    __syncthreads();
+  }
+  const double sgn = (q[iperm[si[0]]] < 0.0) ? -1.0 : 1.0;
+  for (int64_t o = threadIdx.x; o < n; o += blockDim.x) V[(int64_t)j * n + o] = sgn * q[iperm[o]];
+}
+__global__ void k_set_j(State *st, int j) {
+  st->j = j;
+  st->bar = 0u;
+}
+// fixed pseudo-random start vector when the caller passes none
+__global__ void k_default_start(double *x, int64_t n, int j) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t z = (uint64_t)i * 0x9E3779B97F4A7C15ull + (uint64_t)(j + 1) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    x[i] = double(z >> 11) * (1.0 / 9007199254740992.0) - 0.5;
+  }
+}
+
+}  // namespace nle
+
+using namespace nle;
+
+// ---------------------------------------------------------------------------
+// device buffers
+// ---------------------------------------------------------------------------
+namespace {
+
+struct DBuf {
+  void *p = nullptr;
+  size_t bytes = 0;
+  ~DBuf() { reset(); }
+  void reset() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  template <typename X>
+  X *as() const {
+    return reinterpret_cast<X *>(p);
+  }
+};
+
+struct Status {
+  nle_status code;
+  std::string msg;
+};
+
+}  // namespace
+
+struct nle_ctx {
+  int device = 0;
+  int nsm = 0;
+  cudaStream_t stream = nullptr;
+  nle_options opt{};
+  int64_t n = 0, nnz = 0;
+  std::vector<int64_t> rowptr;
+  std::vector<int32_t> col;
+  std::vector<double> val;
+  bool factored = false;
+  Factor F;
+  std::vector<int32_t> perm, iperm;
+  int vw = 4;
+  int64_t npad = 0, nchunks = 0;
+  int grid = 0, rpc = 0;
+  int ldq = 0;
+  // device memory
+  DBuf d_perm, d_iperm;
+  DBuf A_sptr, A_col, A_val, A64_val, L_sptr, L_col, L_val, U_sptr, U_col, U_val, d_diag, d_sub, d_nsub;
+  DBuf vecs;   // working-precision vectors
+  DBuf vec64;  // Au, r, t
+  DBuf dQ, dQt, dS, dR;
+  DBuf part, state;
+  DBuf scratch;  // 2 * n doubles for host transfers
+  std::vector<double> pinned_dummy;
+  bool solved = false;
+  int last_p = 0;
+  std::vector<double> lambda;
+  std::string err;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+};
+
+static thread_local std::string g_create_error;
+
+static nle_status fail(nle_t h, nle_status code, const std::string &msg) {
+  if (h)
+    h->err = msg;
+  else
+    g_create_error = msg;
+  return code;
+}
+
+#define NLE_CUDA(h, call)                                                                  \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess) {                                                               \
+      return fail(h, e_ == cudaErrorMemoryAllocation ? NLE_ERR_OOM : NLE_ERR_CUDA,         \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                     \
+    }                                                                                      \
+  } while (0)
+
+static cudaError_t dalloc(DBuf &b, size_t bytes) {
+  b.reset();
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(&b.p, bytes);
+  if (e == cudaSuccess) {
+    b.bytes = bytes;
+    e = cudaMemset(b.p, 0, bytes);
+  }
+  return e;
+}
+
+template <typename X>
+static cudaError_t upload(DBuf &b, const std::vector<X> &v) {
+  cudaError_t e = dalloc(b, v.size() * sizeof(X));
+  if (e != cudaSuccess) return e;
+  if (!v.empty()) e = cudaMemcpy(b.p, v.data(), v.size() * sizeof(X), cudaMemcpyHostToDevice);
+  return e;
+}
+
+static bool mixed(nle_t h) { return h->opt.precision == NLE_MIXED; }
+
+template <typename T>
+static Dev<T> make_dev(nle_t h) {
+  Dev<T> D;
+  D.n = h->n;
+  D.npad = h->npad;
+  D.nchunks = h->nchunks;
+  D.ldq = h->ldq;
+  const int64_t ns = h->npad / (32 * h->vw);
+  D.A = {ns, h->A_sptr.as<int64_t>(), h->A_col.as<int32_t>(), h->A_val.as<T>()};
+  D.A64 = {ns, h->A_sptr.as<int64_t>(), h->A_col.as<int32_t>(), h->A64_val.as<double>()};
+  D.L = {ns, h->L_sptr.as<int64_t>(), h->L_col.as<int32_t>(), h->L_val.as<T>()};
+  D.U = {ns, h->U_sptr.as<int64_t>(), h->U_col.as<int32_t>(), h->U_val.as<T>()};
+  D.diag = h->d_diag.as<T>();
+  D.sub = h->d_sub.as<uint8_t>();
+  D.nsub = h->d_nsub.as<uint8_t>();
+  const int64_t np = h->npad, ext = h->npad + 32 * h->vw;
+  T *v = h->vecs.as<T>();
+  D.p = v + 0 * np;
+  D.y = v + 1 * np;
+  D.s = v + 2 * np;
+  D.g = v + 3 * np;
+  D.rT = v + 4 * np;
+  D.x = v + 5 * np;
+  D.Ax = v + 6 * np;
+  D.Ap = v + 7 * np;
+  D.z = v + 8 * np;
+  D.c0 = v + 8 * np + ext;
+  double *w = h->vec64.as<double>();
+  D.Au = w;
+  D.r = w + np;
+  D.t = w + 2 * np;
+  D.u = nullptr;
+  D.Q = h->dQ.as<T>();
+  D.Qt = h->dQt.as<double>();
+  D.S = h->dS.as<T>();
+  D.R = h->dR.as<T>();
+  D.part = h->part.as<double>();
+  D.st = h->state.as<State>();
+  return D;
+}
+
+static Opts make_opts(nle_t h, double tol, int max_newton, int max_pcg) {
+  Opts O;
+  O.tol = tol;
+  O.tau_pcg = h->opt.tau_pcg;
+  O.tau_dacg = h->opt.tau_dacg;
+  O.max_newton = max_newton;
+  O.max_pcg = max_pcg;
+  O.max_dacg = h->opt.max_dacg;
+  O.kmax = h->opt.k_max;
+  O.exit_eigres = h->opt.exit_eigres;
+  O.exit_stag = h->opt.exit_stagnation;
+  O.recompute = h->opt.dacg_recompute;
+  O.spin_ns = (long long)(h->opt.spin_timeout_s * 1e9);
+  return O;
+}
+
+// Cooperative launch of kernel `id` (persistent, gridDim = h->grid).
+template <typename T>
+static nle_status launch(nle_t h, int id, void **args) {
+  void *fn = kernel_ptr<T>(id, h->rpc);
+  if (!fn) return fail(h, NLE_ERR_ARG, "no kernel instance for this size");
+  int nb = 0;
+  NLE_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, TPB, 0));
+  if (nb < 1 || h->grid > nb * h->nsm) return fail(h, NLE_ERR_CUDA, "persistent grid does not fit on the device");
+  // reset the grid-barrier counter
+  State *st = h->state.as<State>();
+  NLE_CUDA(h, cudaMemsetAsync(&st->bar, 0, sizeof(unsigned), h->stream));
+  NLE_CUDA(h, cudaLaunchCooperativeKernel(fn, dim3(h->grid), dim3(TPB), args, 0, h->stream));
+  return NLE_OK;
+}
+
+static nle_status check_state_error(nle_t h) {
+  State st;
+  NLE_CUDA(h, cudaMemcpyAsync(&st.err, &h->state.as<State>()->err, 2 * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  NLE_CUDA(h, cudaStreamSynchronize(h->stream));
+  if (st.err != 0) {
+    char buf[128];
+    snprintf(buf, sizeof buf, "device wait ran out (code %d at site %d)", st.err, st.err_where);
+    // clear it so the handle stays usable
+    NLE_CUDA(h, cudaMemsetAsync(&h->state.as<State>()->err, 0, 2 * sizeof(int), h->stream));
+    NLE_CUDA(h, cudaStreamSynchronize(h->stream));
+    return fail(h, (nle_status)st.err, buf);
+  }
+  return NLE_OK;
+}
+
+// Make sure Q / Qt have room for m columns.
+static nle_status ensure_q(nle_t h, int m) {
+  if (m <= h->ldq) return NLE_OK;
+  const size_t tsz = mixed(h) ? 4 : 8;
+  NLE_CUDA(h, dalloc(h->dQ, (size_t)h->npad * m * tsz));
+  NLE_CUDA(h, dalloc(h->dQt, (size_t)h->npad * m * 8));
+  h->ldq = m;
+  return NLE_OK;
+}
+
+// Copy p vectors of length n (natural order, FP64, host or device) into a
+// device array of working-precision columns (level order) at dst + c*npad.
+template <typename T>
+static nle_status put_vectors(nle_t h, const double *src, int count, T *dst, int on_device) {
+  const int64_t n = h->n;
+  for (int c = 0; c < count; c++) {
+    const double *s = src + (int64_t)c * n;
+    if (!on_device) {
+      NLE_CUDA(h, cudaMemcpyAsync(h->scratch.p, s, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+      s = h->scratch.as<double>();
+    }
+    k_gather<T><<<1024, 256, 0, h->stream>>>(dst + (int64_t)c * h->npad, s, h->d_perm.as<int32_t>(), n, h->npad);
+    NLE_CUDA(h, cudaGetLastError());
+  }
+  return NLE_OK;
+}
+
+template <typename T>
+static nle_status get_vector(nle_t h, const T *src, double *dst, int on_device) {
+  double *d = on_device ? dst : h->scratch.as<double>();
+  k_scatter<T><<<1024, 256, 0, h->stream>>>(d, src, h->d_iperm.as<int32_t>(), h->n);
+  NLE_CUDA(h, cudaGetLastError());
+  if (!on_device) NLE_CUDA(h, cudaMemcpyAsync(dst, d, h->n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  return NLE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+void nle_default_options(nle_options *o) {
+  if (!o) return;
+  o->k_max = 5;
+  o->tau_pcg = 1e-2;
+  o->tau_dacg = 1e-2;
+  o->max_dacg = 5000;
+  o->precision = NLE_FP64;
+  o->exit_eigres = 1;
+  o->exit_stagnation = 1;
+  o->dacg_recompute = 50;
+  o->spin_timeout_s = 2.0;
+  o->grid_ctas = 0;
+}
+
+const char *nle_last_error(nle_t h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+void nle_destroy(nle_t h) {
+  if (!h) return;
+  cudaSetDevice(h->device);
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  for (auto &e : h->ev)
+    if (e) cudaEventDestroy(e);
+  delete h;
+}
+
+nle_status nle_create(int64_t n, int64_t nnz, const int64_t *rowptr, const int32_t *col, const double *val,
+                      int on_device, void *stream, const nle_options *opt, nle_t *out) {
+  if (!out) return fail(nullptr, NLE_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (n < 2 || nnz < n || !rowptr || !col || !val) return fail(nullptr, NLE_ERR_ARG, "need n >= 2, nnz >= n and non-NULL CSR arrays");
+  if (n >= (int64_t)1 << 30) return fail(nullptr, NLE_ERR_ARG, "n too large");
+  std::unique_ptr<nle_ctx> h(new nle_ctx);
+  if (opt)
+    h->opt = *opt;
+  else
+    nle_default_options(&h->opt);
+  if (h->opt.k_max < 0 || h->opt.k_max > NLE_MAX_KMAX) return fail(nullptr, NLE_ERR_ARG, "k_max out of range");
+  if (h->opt.precision != NLE_FP64 && h->opt.precision != NLE_MIXED) return fail(nullptr, NLE_ERR_ARG, "bad precision");
+  if (!(h->opt.spin_timeout_s > 0)) return fail(nullptr, NLE_ERR_ARG, "spin_timeout_s must be positive");
+  h->n = n;
+  h->nnz = nnz;
+  h->rowptr.resize(n + 1);
+  h->col.resize(nnz);
+  h->val.resize(nnz);
+  if (on_device) {
+    if (cudaMemcpy(h->rowptr.data(), rowptr, (n + 1) * 8, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(h->col.data(), col, nnz * 4, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(h->val.data(), val, nnz * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
+      return fail(nullptr, NLE_ERR_CUDA, "copy of the CSR arrays failed");
+  } else {
+    memcpy(h->rowptr.data(), rowptr, (n + 1) * 8);
+    memcpy(h->col.data(), col, nnz * 4);
+    memcpy(h->val.data(), val, nnz * 8);
+  }
+  // host-side validation first: it needs no device
+  std::string msg;
+  const int rc = validate_csr(n, nnz, h->rowptr.data(), h->col.data(), h->val.data(), msg);
+  if (rc == 2) return fail(nullptr, NLE_ERR_CSR, msg);
+  if (rc == 3) return fail(nullptr, NLE_ERR_NOT_SPD, msg);
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) return fail(nullptr, NLE_ERR_NO_DEVICE, "no CUDA device");
+  cudaGetDevice(&h->device);
+  cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, h->device);
+  h->stream = (cudaStream_t)stream;
+  h->vw = (h->opt.precision == NLE_MIXED) ? 4 : 2;
+  for (auto &e : h->ev)
+    if (cudaEventCreate(&e) != cudaSuccess) return fail(nullptr, NLE_ERR_CUDA, "cudaEventCreate failed");
+  *out = h.release();
+  return NLE_OK;
+}
+
+nle_status nle_factor_ic(nle_t h, int lfil, double tau_ic) {
+  if (!h) return fail(nullptr, NLE_ERR_ARG, "NULL handle");
+  if (lfil < 0 || !(tau_ic >= 0.0)) return fail(h, NLE_ERR_ARG, "need lfil >= 0 and tau_ic >= 0");
+  cudaSetDevice(h->device);
+  h->factored = false;
+  h->solved = false;
+  int64_t bad = -1;
+  Factor F;
+  if (ic_factor_host(h->n, h->rowptr.data(), h->col.data(), h->val.data(), lfil, tau_ic, F, &bad) != 0)
+    return fail(h, NLE_ERR_NOT_SPD, "non-positive pivot in IC column " + std::to_string(bad));
+  h->F = std::move(F);
+  level_order(h->F, h->perm, h->iperm);
+  const int H = 32 * h->vw;
+  h->npad = ((h->n + H - 1) / H) * H;
+  h->nchunks = h->npad / h->vw;
+  // persistent grid: one CTA per SM, fewer for small problems
+  int grid = h->opt.grid_ctas > 0 ? h->opt.grid_ctas : h->nsm;
+  const int64_t need = (h->nchunks + TPB - 1) / TPB;
+  grid = (int)std::max<int64_t>(1, std::min<int64_t>(grid, need));
+  int rpc = 0;
+  for (int r : {1, 2, 4, 8})
+    if ((int64_t)r * grid * TPB >= h->nchunks) {
+      rpc = r;
+      break;
+    }
+  if (!rpc) return fail(h, NLE_ERR_ARG, "n too large for one persistent grid");
+  h->grid = grid;
+  h->rpc = rpc;
+  Permuted P;
+  permute(h->n, h->rowptr.data(), h->col.data(), h->val.data(), h->F, h->perm, h->iperm, h->npad, P);
+  const size_t tsz = mixed(h) ? 4 : 8;
+  if (mixed(h)) {
+    SellSet<float> S;
+    build_sell<float>(P, H, S);
+    NLE_CUDA(h, upload(h->A_sptr, S.A.sptr));
+    NLE_CUDA(h, upload(h->A_col, S.A.col));
+    NLE_CUDA(h, upload(h->A_val, S.A.val));
+    NLE_CUDA(h, upload(h->A64_val, S.A64.val));
+    NLE_CUDA(h, upload(h->L_sptr, S.L.sptr));
+    NLE_CUDA(h, upload(h->L_col, S.L.col));
+    NLE_CUDA(h, upload(h->L_val, S.L.val));
+    NLE_CUDA(h, upload(h->U_sptr, S.U.sptr));
+    NLE_CUDA(h, upload(h->U_col, S.U.col));
+    NLE_CUDA(h, upload(h->U_val, S.U.val));
+    NLE_CUDA(h, upload(h->d_diag, S.diag));
+    NLE_CUDA(h, upload(h->d_sub, S.sub));
+    NLE_CUDA(h, upload(h->d_nsub, S.nsub));
+  } else {
+    SellSet<double> S;
+    build_sell<double>(P, H, S);
+    NLE_CUDA(h, upload(h->A_sptr, S.A.sptr));
+    NLE_CUDA(h, upload(h->A_col, S.A.col));
+    NLE_CUDA(h, upload(h->A_val, S.A.val));
+    NLE_CUDA(h, upload(h->A64_val, S.A64.val));
+    NLE_CUDA(h, upload(h->L_sptr, S.L.sptr));
+    NLE_CUDA(h, upload(h->L_col, S.L.col));
+    NLE_CUDA(h, upload(h->L_val, S.L.val));
+    NLE_CUDA(h, upload(h->U_sptr, S.U.sptr));
+    NLE_CUDA(h, upload(h->U_col, S.U.col));
+    NLE_CUDA(h, upload(h->U_val, S.U.val));
+    NLE_CUDA(h, upload(h->d_diag, S.diag));
+    NLE_CUDA(h, upload(h->d_sub, S.sub));
+    NLE_CUDA(h, upload(h->d_nsub, S.nsub));
+  }
+  NLE_CUDA(h, upload(h->d_perm, h->perm));
+  NLE_CUDA(h, upload(h->d_iperm, h->iperm));
+  const int64_t ext = h->npad + 32 * h->vw;
+  NLE_CUDA(h, dalloc(h->vecs, (size_t)(8 * h->npad + 2 * ext) * tsz));
+  NLE_CUDA(h, dalloc(h->vec64, (size_t)3 * h->npad * 8));
+  NLE_CUDA(h, dalloc(h->dS, (size_t)h->npad * KMAX * tsz));
+  NLE_CUDA(h, dalloc(h->dR, (size_t)h->npad * KMAX * tsz));
+  NLE_CUDA(h, dalloc(h->part, (size_t)2 * RED_MAX * h->grid * 8));
+  NLE_CUDA(h, dalloc(h->state, sizeof(State)));
+  NLE_CUDA(h, dalloc(h->scratch, (size_t)2 * h->n * 8));
+  h->ldq = 0;
+  nle_status s = ensure_q(h, 8);
+  if (s != NLE_OK) return s;
+  h->factored = true;
+  return NLE_OK;
+}
+
+nle_status nle_get_factor(nle_t h, int64_t *nnzL, int64_t *Lrowptr, int32_t *Lcol, double *Lval, int32_t *levL,
+                          int32_t *levU, int64_t *nlevL, int64_t *nlevU) {
+  if (!h) return fail(nullptr, NLE_ERR_ARG, "NULL handle");
+  if (!h->factored) return fail(h, NLE_ERR_STATE, "nle_factor_ic has not been called");
+  const Factor &F = h->F;
+  if (nnzL) *nnzL = (int64_t)F.Lcol.size();
+  if (Lrowptr) memcpy(Lrowptr, F.Lrowptr.data(), (h->n + 1) * 8);
+  if (Lcol) memcpy(Lcol, F.Lcol.data(), F.Lcol.size() * 4);
+  if (Lval) memcpy(Lval, F.Lval.data(), F.Lval.size() * 8);
+  if (levL) memcpy(levL, F.levL.data(), h->n * 4);
+  if (levU) memcpy(levU, F.levU.data(), h->n * 4);
+  if (nlevL) *nlevL = F.nlevL;
+  if (nlevU) *nlevU = F.nlevU;
+  return NLE_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// solve
+// ---------------------------------------------------------------------------
+template <typename T>
+static nle_status solve_impl(nle_t h, int p, double tol, int max_newton, int max_pcg, const double *X0,
+                             double *lambda, double *V, nle_stats *stats, int on_dev) {
+  nle_status s = ensure_q(h, p);
+  if (s != NLE_OK) return s;
+  Dev<T> D = make_dev<T>(h);
+  Opts O = make_opts(h, tol, max_newton, max_pcg);
+  NLE_CUDA(h, cudaMemsetAsync(h->state.p, 0, sizeof(State), h->stream));
+  double ms_dacg = 0.0, ms_newton = 0.0;
+  int64_t launches = 0;
+  for (int j = 0; j < p; j++) {
+    launches += X0 ? 4 : 5;
+    k_set_j<<<1, 1, 0, h->stream>>>(D.st, j);
+    NLE_CUDA(h, cudaGetLastError());
+    if (X0) {
+      s = put_vectors<T>(h, X0 + (int64_t)j * h->n, 1, D.x, on_dev);
+      if (s != NLE_OK) return s;
+    } else {
+      k_default_start<<<1024, 256, 0, h->stream>>>(h->scratch.as<double>(), h->n, j);
+      s = put_vectors<T>(h, h->scratch.as<double>(), 1, D.x, 1);
+      if (s != NLE_OK) return s;
+    }
+    void *args[] = {&D, &O};
+    NLE_CUDA(h, cudaEventRecord(h->ev[0], h->stream));
+    s = launch<T>(h, K_DACG, args);
+    if (s != NLE_OK) return s;
+    NLE_CUDA(h, cudaEventRecord(h->ev[1], h->stream));
+    s = launch<T>(h, K_NEWTON, args);
+    if (s != NLE_OK) return s;
+    NLE_CUDA(h, cudaEventRecord(h->ev[2], h->stream));
+    NLE_CUDA(h, cudaEventSynchronize(h->ev[2]));
+    float a = 0.f, b = 0.f;
+    cudaEventElapsedTime(&a, h->ev[0], h->ev[1]);
+    cudaEventElapsedTime(&b, h->ev[1], h->ev[2]);
+    ms_dacg += a;
+    ms_newton += b;
+    s = check_state_error(h);
+    if (s != NLE_OK) return s;
+  }
+  // outputs
+  State st;
+  NLE_CUDA(h, cudaMemcpyAsync(&st, h->state.p, sizeof(State), cudaMemcpyDeviceToHost, h->stream));
+  double *vout = on_dev ? V : nullptr;
+  DBuf tmp;
+  if (!on_dev) {
+    NLE_CUDA(h, dalloc(tmp, (size_t)p * h->n * 8));
+    vout = tmp.as<double>();
+  }
+  k_output_vectors<<<p, 1024, 0, h->stream>>>(vout, D.Qt, h->d_iperm.as<int32_t>(), h->n, h->npad);
+  launches++;
+  NLE_CUDA(h, cudaGetLastError());
+  if (!on_dev) NLE_CUDA(h, cudaMemcpyAsync(V, vout, (size_t)p * h->n * 8, cudaMemcpyDeviceToHost, h->stream));
+  NLE_CUDA(h, cudaStreamSynchronize(h->stream));
+  if (on_dev)
+    NLE_CUDA(h, cudaMemcpy(lambda, st.lambda, p * sizeof(double), cudaMemcpyHostToDevice));
+  else
+    memcpy(lambda, st.lambda, p * sizeof(double));
+  h->lambda.assign(st.lambda, st.lambda + p);
+  h->solved = true;
+  h->last_p = p;
+  bool allconv = true, asc = true;
+  for (int j = 0; j < p; j++) {
+    allconv = allconv && st.conv[j];
+    if (j > 0 && !(st.lambda[j] > st.lambda[j - 1])) asc = false;
+  }
+  if (stats) {
+    memset(stats, 0, sizeof(*stats));
+    stats->p = p;
+    for (int j = 0; j < p; j++) {
+      stats->dacg_its[j] = st.dacg_its[j];
+      stats->outer_its[j] = st.outer_its[j];
+      stats->pcg_its[j] = st.pcg_its[j];
+      stats->converged[j] = st.conv[j];
+      stats->final_res[j] = st.res[j];
+    }
+    stats->mvp_dacg = st.mvp_dacg;
+    stats->mvp_newton = st.mvp_newton;
+    for (int e = 0; e < 5; e++) stats->exit_count[e] = st.exits[e];
+    stats->ms_dacg = ms_dacg;
+    stats->ms_newton = ms_newton;
+    stats->pcg_iterations = st.pcg_total;
+    stats->pcg_sum_m = st.pcg_sum_m;
+    stats->pcg_sum_k = st.pcg_sum_k;
+    stats->dacg_iterations = st.dacg_total;
+    stats->dacg_sum_m = st.dacg_sum_m;
+    stats->kernel_launches = launches;
+    stats->ascending = asc ? 1 : 0;
+  }
+  if (!allconv) return fail(h, NLE_ERR_NOCONV, "some eigenpairs reached max_newton");
+  return NLE_OK;
+}
+
+extern "C" nle_status nle_solve(nle_t h, int p, double tol, int max_newton, int max_pcg, const double *X0,
+                                double *lambda, double *V, nle_stats *stats, int buffers_on_device) {
+  if (!h) return fail(nullptr, NLE_ERR_ARG, "NULL handle");
+  if (!h->factored) return fail(h, NLE_ERR_STATE, "nle_factor_ic has not been called");
+  if (p < 1 || p >= h->n || p > NLE_MAX_P || !(tol > 0) || max_newton < 0 || max_pcg < 1 || !lambda || !V)
+    return fail(h, NLE_ERR_ARG, "bad nle_solve arguments");
+  cudaSetDevice(h->device);
+  return mixed(h) ? solve_impl<float>(h, p, tol, max_newton, max_pcg, X0, lambda, V, stats, buffers_on_device)
+                  : solve_impl<double>(h, p, tol, max_newton, max_pcg, X0, lambda, V, stats, buffers_on_device);
+}
+
+// ---------------------------------------------------------------------------
+// building blocks
+// ---------------------------------------------------------------------------
+template <typename T>
+static nle_status shifted_impl(nle_t h, double theta, const double *x, double *y, int on_dev) {
+  Dev<T> D = make_dev<T>(h);
+  nle_status s = put_vectors<T>(h, x, 1, D.p, on_dev);
+  if (s != NLE_OK) return s;
+  void *fn = kernel_ptr<T>(K_SHIFTED, h->rpc);
+  void *args[] = {&D, &theta};
+  NLE_CUDA(h, cudaLaunchKernel(fn, dim3(h->grid), dim3(TPB), args, 0, h->stream));
+  s = get_vector<T>(h, D.y, y, on_dev);
+  if (s != NLE_OK) return s;
+  NLE_CUDA(h, cudaStreamSynchronize(h->stream));
+  return NLE_OK;
+}
+
+extern "C" nle_status nle_apply_shifted(nle_t h, double theta, const double *x, double *y, int buffers_on_device) {
+  if (!h) return fail(nullptr, NLE_ERR_ARG, "NULL handle");
+  if (!h->factored) return fail(h, NLE_ERR_STATE, "nle_factor_ic has not been called");
+  if (!x || !y) return fail(h, NLE_ERR_ARG, "NULL vector");
+  cudaSetDevice(h->device);
+  return mixed(h) ? shifted_impl<float>(h, theta, x, y, buffers_on_device)
+                  : shifted_impl<double>(h, theta, x, y, buffers_on_device);
+}
+
+template <typename T>
+static nle_status prec_impl(nle_t h, int k, const double *S, const double *R, int m, const double *Q, const double *g,
+                            double *c, int on_dev) {
+  nle_status s = ensure_q(h, std::max(m, 1));
+  if (s != NLE_OK) return s;
+  Dev<T> D = make_dev<T>(h);
+  if (k > 0) {
+    if ((s = put_vectors<T>(h, S, k, D.S, on_dev)) != NLE_OK) return s;
+    if ((s = put_vectors<T>(h, R, k, D.R, on_dev)) != NLE_OK) return s;
+  }
+  if (m > 0 && (s = put_vectors<T>(h, Q, m, D.Q, on_dev)) != NLE_OK) return s;
+  if ((s = put_vectors<T>(h, g, 1, D.g, on_dev)) != NLE_OK) return s;
+  Opts O = make_opts(h, 1e-8, 1, 1);
+  NLE_CUDA(h, cudaMemsetAsync(h->state.p, 0, sizeof(State), h->stream));
+  void *args[] = {&D, &O, &m, &k};
+  if ((s = launch<T>(h, K_PREC, args)) != NLE_OK) return s;
+  if ((s = check_state_error(h)) != NLE_OK) return s;
+  if ((s = get_vector<T>(h, D.y, c, on_dev)) != NLE_OK) return s;
+  NLE_CUDA(h, cudaStreamSynchronize(h->stream));
+  return NLE_OK;
+}
+
+extern "C" nle_status nle_apply_prec(nle_t h, int k, const double *S, const double *R, int m, const double *Q,
+                                     const double *g, double *c, int buffers_on_device) {
+  if (!h) return fail(nullptr, NLE_ERR_ARG, "NULL handle");
+  if (!h->factored) return fail(h, NLE_ERR_STATE, "nle_factor_ic has not been called");
+  if (k < 0 || k > NLE_MAX_KMAX || m < 0 || m > NLE_MAX_P || !g || !c || (k > 0 && (!S || !R)) || (m > 0 && !Q))
+    return fail(h, NLE_ERR_ARG, "bad nle_apply_prec arguments");
+  cudaSetDevice(h->device);
+  return mixed(h) ? prec_impl<float>(h, k, S, R, m, Q, g, c, buffers_on_device)
+                  : prec_impl<double>(h, k, S, R, m, Q, g, c, buffers_on_device);
+}
+
+template <typename T>
+static nle_status pcg_impl(nle_t h, double theta, double tol, int max_pcg, const double *r, int m, const double *Q,
+                           int k, const double *S, const double *R, double *sout, nle_pcg_info *info, int on_dev) {
+  nle_status s = ensure_q(h, m);
+  if (s != NLE_OK) return s;
+  Dev<T> D = make_dev<T>(h);
+  if (k > 0) {
+    if ((s = put_vectors<T>(h, S, k, D.S, on_dev)) != NLE_OK) return s;
+    if ((s = put_vectors<T>(h, R, k, D.R, on_dev)) != NLE_OK) return s;
+  }
+  if ((s = put_vectors<T>(h, Q, m, D.Q, on_dev)) != NLE_OK) return s;
+  if ((s = put_vectors<T>(h, r, 1, D.rT, on_dev)) != NLE_OK) return s;
+  Opts O = make_opts(h, tol, 1, max_pcg);
+  NLE_CUDA(h, cudaMemsetAsync(h->state.p, 0, sizeof(State), h->stream));
+  void *args[] = {&D, &O, &m, &k, &theta, &max_pcg};
+  if ((s = launch<T>(h, K_PCG, args)) != NLE_OK) return s;
+  if ((s = check_state_error(h)) != NLE_OK) return s;
+  if ((s = get_vector<T>(h, D.s, sout, on_dev)) != NLE_OK) return s;
+  State st;
+  NLE_CUDA(h, cudaMemcpyAsync(&st, h->state.p, sizeof(State), cudaMemcpyDeviceToHost, h->stream));
+  NLE_CUDA(h, cudaStreamSynchronize(h->stream));
+  if (info) {
+    info->its = st.last_its;
+    info->exit = st.last_exit;
+    info->gnorm0 = st.last_g0;
+    info->gnorm = st.last_gn;
+    info->eigres = st.last_eres;
+  }
+  return NLE_OK;
+}
+
+extern "C" nle_status nle_pcg(nle_t h, double theta, double tol, int max_pcg, const double *r, int m, const double *Q,
+                              int k, const double *S, const double *R, double *s, nle_pcg_info *info,
+                              int buffers_on_device) {
+  if (!h) return fail(nullptr, NLE_ERR_ARG, "NULL handle");
+  if (!h->factored) return fail(h, NLE_ERR_STATE, "nle_factor_ic has not been called");
+  if (m < 1 || m > NLE_MAX_P || k < 0 || k > NLE_MAX_KMAX || max_pcg < 1 || !r || !Q || !s ||
+      (k > 0 && (!S || !R)))
+    return fail(h, NLE_ERR_ARG, "bad nle_pcg arguments");
+  cudaSetDevice(h->device);
+  return mixed(h) ? pcg_impl<float>(h, theta, tol, max_pcg, r, m, Q, k, S, R, s, info, buffers_on_device)
+                  : pcg_impl<double>(h, theta, tol, max_pcg, r, m, Q, k, S, R, s, info, buffers_on_device);
+}
+
+extern "C" nle_status nle_backward(nle_t h, const double *gbar_lambda, const double *gbar_V, double *grad_val,
+                                   int buffers_on_device) {
+  if (!h) return fail(nullptr, NLE_ERR_ARG, "NULL handle");
+  if (!h->solved) return fail(h, NLE_ERR_STATE, "nle_solve has not completed");
+  (void)gbar_lambda;
+  (void)gbar_V;
+  (void)grad_val;
+  (void)buffers_on_device;
+  return fail(h, NLE_ERR_STATE, "nle_backward is not available in this build");
+}
+
+extern "C" nle_status nle_batch_solve(int count, nle_t *hs, int p, double tol, int max_newton, int max_pcg,
+                                      const double *const *X0s, double *const *lambdas, double *const *Vs,
+                                      nle_status *per_problem) {
+  if (count < 1 || !hs || !lambdas || !Vs) return fail(nullptr, NLE_ERR_ARG, "bad nle_batch_solve arguments");
+  nle_status worst = NLE_OK;
+  for (int b = 0; b < count; b++) {
+    nle_status s = nle_solve(hs[b], p, tol, max_newton, max_pcg, X0s ? X0s[b] : nullptr, lambdas[b], Vs[b], nullptr, 1);
+    if (per_problem) per_problem[b] = s;
+    if (s != NLE_OK && (worst == NLE_OK || s != NLE_ERR_NOCONV)) worst = s;
+  }
+  return worst;
+}

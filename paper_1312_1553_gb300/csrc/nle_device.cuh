@@ -1,0 +1,421 @@
+// Device primitives of the persistent solver kernels: vector loads, bounded
+// grid barrier, deterministic block/grid reductions, SELL SpMV and the
+// sync-free triangular solves.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "nle_internal.h"
+
+namespace nle {
+
+// ---------------------------------------------------------------------------
+// precision traits: VW rows per thread so that one row group is 16 bytes
+// ---------------------------------------------------------------------------
+template <typename T>
+struct VT;
+template <>
+struct VT<float> {
+  static constexpr int W = 4;
+};
+template <>
+struct VT<double> {
+  static constexpr int W = 2;
+};
+
+// Coherent (L2) vector loads of W consecutive elements of a vector that is
+// written inside the kernel; read-only loads (__ldg) for the matrices.
+__device__ __forceinline__ void ldc(const float *p, float (&o)[4]) {
+  float4 v = __ldcg(reinterpret_cast<const float4 *>(p));
+  o[0] = v.x, o[1] = v.y, o[2] = v.z, o[3] = v.w;
+}
+__device__ __forceinline__ void ldc(const double *p, double (&o)[2]) {
+  double2 v = __ldcg(reinterpret_cast<const double2 *>(p));
+  o[0] = v.x, o[1] = v.y;
+}
+__device__ __forceinline__ void ldc(const double *p, double (&o)[4]) {
+  double2 a = __ldcg(reinterpret_cast<const double2 *>(p));
+  double2 b = __ldcg(reinterpret_cast<const double2 *>(p + 2));
+  o[0] = a.x, o[1] = a.y, o[2] = b.x, o[3] = b.y;
+}
+__device__ __forceinline__ void stv(float *p, const float (&o)[4]) {
+  __stcg(reinterpret_cast<float4 *>(p), make_float4(o[0], o[1], o[2], o[3]));
+}
+__device__ __forceinline__ void stv(double *p, const double (&o)[2]) {
+  __stcg(reinterpret_cast<double2 *>(p), make_double2(o[0], o[1]));
+}
+__device__ __forceinline__ void stv(double *p, const double (&o)[4]) {
+  __stcg(reinterpret_cast<double2 *>(p), make_double2(o[0], o[1]));
+  __stcg(reinterpret_cast<double2 *>(p + 2), make_double2(o[2], o[3]));
+}
+__device__ __forceinline__ void ldr(const float *p, float (&o)[4]) {
+  float4 v = __ldg(reinterpret_cast<const float4 *>(p));
+  o[0] = v.x, o[1] = v.y, o[2] = v.z, o[3] = v.w;
+}
+__device__ __forceinline__ void ldr(const double *p, double (&o)[2]) {
+  double2 v = __ldg(reinterpret_cast<const double2 *>(p));
+  o[0] = v.x, o[1] = v.y;
+}
+__device__ __forceinline__ void ldr(const double *p, double (&o)[4]) {
+  double2 a = __ldg(reinterpret_cast<const double2 *>(p));
+  double2 b = __ldg(reinterpret_cast<const double2 *>(p + 2));
+  o[0] = a.x, o[1] = a.y, o[2] = b.x, o[3] = b.y;
+}
+__device__ __forceinline__ void ldr(const int32_t *p, int (&o)[4]) {
+  int4 v = __ldg(reinterpret_cast<const int4 *>(p));
+  o[0] = v.x, o[1] = v.y, o[2] = v.z, o[3] = v.w;
+}
+__device__ __forceinline__ void ldr(const int32_t *p, int (&o)[2]) {
+  int2 v = __ldg(reinterpret_cast<const int2 *>(p));
+  o[0] = v.x, o[1] = v.y;
+}
+
+// ---------------------------------------------------------------------------
+// memory-model helpers (PTX): relaxed gpu-scope loads/stores bypass L1 and
+// observe other SMs' stores; acquire/release for the grid barrier.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float ld_relaxed(const float *p) {
+  float v;
+  asm volatile("ld.relaxed.gpu.global.f32 %0, [%1];" : "=f"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ double ld_relaxed(const double *p) {
+  double v;
+  asm volatile("ld.relaxed.gpu.global.f64 %0, [%1];" : "=d"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_relaxed(float *p, float v) {
+  asm volatile("st.relaxed.gpu.global.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
+}
+__device__ __forceinline__ void st_relaxed(double *p, double v) {
+  asm volatile("st.relaxed.gpu.global.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
+}
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ int ld_relaxed_int(const int *p) {
+  int v;
+  asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void red_release_add(unsigned *p, unsigned v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ long long gtimer() {
+  long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Not-yet-computed marker of the triangular solves: a NaN payload that GPU
+// arithmetic never produces (it returns the canonical NaN 0x7fffffff).
+__device__ __forceinline__ bool is_sent(float v) { return __float_as_uint(v) == 0xFFC0BAD1u; }
+__device__ __forceinline__ bool is_sent(double v) {
+  return __double_as_longlong(v) == (long long)0xFFF8BAD1BAD1BAD1ull;
+}
+template <typename T>
+__device__ __forceinline__ T sentinel();
+template <>
+__device__ __forceinline__ float sentinel<float>() {
+  return __uint_as_float(0xFFC0BAD1u);
+}
+template <>
+__device__ __forceinline__ double sentinel<double>() {
+  return __longlong_as_double((long long)0xFFF8BAD1BAD1BAD1ull);
+}
+
+__device__ __forceinline__ void record_error(State *st, int code, int where) {
+  if (atomicCAS(&st->err, 0, code) == 0) st->err_where = where;
+}
+
+// ---------------------------------------------------------------------------
+// per-CTA shared state
+// ---------------------------------------------------------------------------
+struct Shared {
+  double red[NWARP][RED_MAX];  // warp partial sums of the current pass
+  double sc[RED_MAX];          // grid-reduced scalars of the last pass
+  double a[KMAX], b[KMAX], ab[KMAX];
+  double sg[KMAX];             // S^T g
+  double alpha[KMAX];          // s_s^T r_s (chronological)
+  double gsr[KMAX][KMAX];      // s_s^T r_t
+  double gqs[MMAX][KMAX];      // q_c^T s_t
+  double zq[MMAX];             // Q^T c (Algorithm 3.1, last two steps)
+  double qv[MMAX];             // Q^T v of the current projection
+  int order[KMAX];             // chronological -> physical pair slot
+  int ok;                      // error word broadcast after each barrier
+};
+
+struct Ctl {
+  unsigned epoch;  // barriers passed by this CTA (thread 0 only)
+  int rbuf;        // reduction buffer parity
+  long long spin_ns;
+};
+
+// Grid-wide barrier for a cooperative launch.  Monotone counter: barrier
+// number e completes when the counter reaches e * gridDim.x.  Every wait is
+// bounded: after spin_ns without progress, or when another CTA already
+// recorded an error, the CTA records NLE_ERR_TIMEOUT (first error wins) and
+// leaves the barrier.  Returns false when the solver must stop.
+__device__ __forceinline__ bool grid_sync(State *st, Shared &sh, Ctl &ctl, int where) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ctl.epoch++;
+    const unsigned target = ctl.epoch * gridDim.x;
+    __threadfence();
+    red_release_add(&st->bar, 1u);
+    long long t0 = 0;
+    int spins = 0;
+    while (ld_acquire(&st->bar) < target) {
+      if (++spins >= 32) {
+        spins = 0;
+        if (ld_relaxed_int(&st->err) != 0) break;
+        const long long now = gtimer();
+        if (t0 == 0)
+          t0 = now;
+        else if (now - t0 > ctl.spin_ns) {
+          record_error(st, 8 /*NLE_ERR_TIMEOUT*/, where);
+          break;
+        }
+      }
+    }
+    __threadfence();
+    sh.ok = (ld_relaxed_int(&st->err) == 0);
+  }
+  __syncthreads();
+  return sh.ok != 0;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Deterministic reductions.  Every warp of every CTA calls red_put for the
+// same slots in the same order; red_flush writes the CTA's sums; after a
+// grid barrier red_collect sums the CTAs' partials in CTA order, so every
+// CTA obtains bit-identical scalars and takes the same control decisions.
+__device__ __forceinline__ void red_put(Shared &sh, int slot, double v) {
+  v = warp_sum(v);
+  if ((threadIdx.x & 31) == 0) sh.red[threadIdx.x >> 5][slot] = v;
+}
+
+template <typename T>
+__device__ __forceinline__ void red_flush(const Dev<T> &D, Shared &sh, Ctl &ctl, int nslots) {
+  __syncthreads();
+  double *part = D.part + (size_t)ctl.rbuf * RED_MAX * gridDim.x;
+  for (int s = threadIdx.x; s < nslots; s += TPB) {
+    double v = 0.0;
+#pragma unroll
+    for (int w = 0; w < NWARP; w++) v += sh.red[w][s];
+    part[(size_t)s * gridDim.x + blockIdx.x] = v;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void red_collect(const Dev<T> &D, Shared &sh, Ctl &ctl, int nslots) {
+  const double *part = D.part + (size_t)ctl.rbuf * RED_MAX * gridDim.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int s = warp; s < nslots; s += NWARP) {
+    double v = 0.0;
+    for (int b = lane; b < (int)gridDim.x; b += 32) v += __ldcg(part + (size_t)s * gridDim.x + b);
+    v = warp_sum(v);
+    if (lane == 0) sh.sc[s] = v;
+  }
+  ctl.rbuf ^= 1;
+  __syncthreads();
+}
+
+// flush + barrier + collect
+template <typename T>
+__device__ __forceinline__ bool reduce_all(const Dev<T> &D, Shared &sh, Ctl &ctl, int nslots, int where) {
+  red_flush(D, sh, ctl, nslots);
+  if (!grid_sync(D.st, sh, ctl, where)) return false;
+  red_collect(D, sh, ctl, nslots);
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// row ownership: thread t owns row groups ("chunks") t, t+TT, t+2TT, ...;
+// chunk c holds rows c*W .. c*W+W-1.  Backward sweeps use the mirrored
+// numbering nchunks-1-(t + i TT).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int64_t gtid() { return (int64_t)blockIdx.x * TPB + threadIdx.x; }
+__device__ __forceinline__ int64_t gthreads() { return (int64_t)gridDim.x * TPB; }
+
+// y[v] = sum_e val * x[col] for the W rows of one chunk of a SELL matrix.
+template <int W, typename TV, typename TX, typename TA>
+__device__ __forceinline__ void sell_rows(const Sell<TV> &M, const TX *__restrict__ x, int64_t chunk,
+                                          TA (&acc)[W]) {
+  constexpr int H = 32 * W;
+  const int64_t slice = chunk >> 5;
+  const int lanepos = (int)(chunk & 31);
+  const int64_t base = __ldg(M.sptr + slice);
+  const int width = (int)((__ldg(M.sptr + slice + 1) - base) / H);
+#pragma unroll
+  for (int v = 0; v < W; v++) acc[v] = TA(0);
+  const int64_t off0 = base + (int64_t)lanepos * W;
+  int e = 0;
+  for (; e + 2 <= width; e += 2) {
+    int c0[W], c1[W];
+    TV a0[W], a1[W];
+    ldr(M.col + off0 + (int64_t)e * H, c0);
+    ldr(M.col + off0 + (int64_t)(e + 1) * H, c1);
+    ldr(M.val + off0 + (int64_t)e * H, a0);
+    ldr(M.val + off0 + (int64_t)(e + 1) * H, a1);
+    TX x0[W], x1[W];
+#pragma unroll
+    for (int v = 0; v < W; v++) {
+      x0[v] = __ldcg(x + c0[v]);
+      x1[v] = __ldcg(x + c1[v]);
+    }
+#pragma unroll
+    for (int v = 0; v < W; v++) {
+      acc[v] += TA(a0[v]) * TA(x0[v]);
+      acc[v] += TA(a1[v]) * TA(x1[v]);
+    }
+  }
+  if (e < width) {
+    int c0[W];
+    TV a0[W];
+    ldr(M.col + off0 + (int64_t)e * H, c0);
+    ldr(M.val + off0 + (int64_t)e * H, a0);
+#pragma unroll
+    for (int v = 0; v < W; v++) acc[v] += TA(a0[v]) * TA(__ldcg(x + c0[v]));
+  }
+}
+
+// Wait (bounded) for a solve output to leave the not-yet-computed state.
+template <typename T>
+__device__ __noinline__ T spin_value(const T *p, T v, State *st, long long spin_ns) {
+  const long long t0 = gtimer();
+  while (is_sent(v)) {
+    v = ld_relaxed(p);
+    if (is_sent(v) && gtimer() - t0 > spin_ns) {
+      record_error(st, 8 /*NLE_ERR_TIMEOUT*/, 100);
+      return T(0);
+    }
+  }
+  return v;
+}
+
+// One chunk of a sync-free triangular solve.  LOWER: dependencies of row r
+// are positions < r; otherwise positions > r (the mirrored sweep).
+// Rows are in level order, so a slice (the 32 chunks of one warp) holds a
+// run of consecutive levels; sub[row] is the level of the row minus the
+// lowest level in its slice and nsub[slice] the number of levels in it.
+// The warp handles the levels of its slice in rounds (ascending for the
+// lower solve, descending for the upper one) separated by __syncwarp, so a
+// lane never waits for another lane of its own warp: dependencies inside
+// the slice were published in an earlier round, dependencies inside the
+// chunk come from registers, and only rows of other warps are polled.
+template <bool LOWER, typename T>
+__device__ __forceinline__ void solve_chunk(const Sell<T> &M, const T *__restrict__ diag,
+                                            const uint8_t *__restrict__ sub, const uint8_t *__restrict__ nsub,
+                                            T *xvec, int64_t chunk, const T (&rhs)[VT<T>::W],
+                                            T (&xsol)[VT<T>::W], State *st, long long spin_ns) {
+  constexpr int W = VT<T>::W;
+  constexpr int H = 32 * W;
+  const int64_t slice = chunk >> 5;
+  const int lanepos = (int)(chunk & 31);
+  const int64_t base = __ldg(M.sptr + slice);
+  const int width = (int)((__ldg(M.sptr + slice + 1) - base) / H);
+  const int64_t r0 = chunk * W;
+  const int rounds = __ldg(nsub + slice);
+  int rs[W];
+#pragma unroll
+  for (int v = 0; v < W; v++) rs[v] = __ldg(sub + r0 + v);
+  const int64_t off0 = base + (int64_t)lanepos * W;
+  T dg[W];
+  ldr(diag + r0, dg);
+  for (int rr = 0; rr < rounds; rr++) {
+    const int rnd = LOWER ? rr : rounds - 1 - rr;
+    bool act[W];
+    bool any = false;
+#pragma unroll
+    for (int v = 0; v < W; v++) {
+      act[v] = (rs[v] == rnd);
+      any = any || act[v];
+    }
+    if (any) {
+      T acc[W];
+      T cin[W][W];  // coupling to rows of the same chunk: cin[v][d] multiplies x[r0+d]
+#pragma unroll
+      for (int v = 0; v < W; v++) {
+        acc[v] = rhs[v];
+#pragma unroll
+        for (int d = 0; d < W; d++) cin[v][d] = T(0);
+      }
+      for (int e0 = 0; e0 < width; e0 += 2) {
+        int cc[2][W];
+        T aa[2][W];
+        T xx[2][W];
+        const bool two = (e0 + 1 < width);
+        ldr(M.col + off0 + (int64_t)e0 * H, cc[0]);
+        ldr(M.val + off0 + (int64_t)e0 * H, aa[0]);
+        if (two) {
+          ldr(M.col + off0 + (int64_t)(e0 + 1) * H, cc[1]);
+          ldr(M.val + off0 + (int64_t)(e0 + 1) * H, aa[1]);
+        } else {
+#pragma unroll
+          for (int v = 0; v < W; v++) cc[1][v] = cc[0][v], aa[1][v] = T(0);
+        }
+        // issue every external load first, then wait for the ones not ready
+#pragma unroll
+        for (int q = 0; q < 2; q++)
+#pragma unroll
+          for (int v = 0; v < W; v++) {
+            const int64_t c = cc[q][v];
+            const bool inside = (c >= r0 && c < r0 + W);
+            xx[q][v] = (inside || !act[v]) ? T(0) : ld_relaxed(xvec + c);
+          }
+#pragma unroll
+        for (int q = 0; q < 2; q++)
+#pragma unroll
+          for (int v = 0; v < W; v++) {
+            if (!act[v]) continue;
+            const int64_t c = cc[q][v];
+            const bool inside = (c >= r0 && c < r0 + W);
+            if (inside) {
+#pragma unroll
+              for (int d = 0; d < W; d++)
+                if (c - r0 == d) cin[v][d] += aa[q][v];
+            } else {
+              T xv = xx[q][v];
+              if (is_sent(xv)) xv = spin_value(xvec + c, xv, st, spin_ns);
+              acc[v] -= aa[q][v] * xv;
+            }
+          }
+      }
+      if (LOWER) {
+#pragma unroll
+        for (int v = 0; v < W; v++) {
+          if (!act[v]) continue;
+          T t = acc[v];
+#pragma unroll
+          for (int d = 0; d < W; d++)
+            if (d < v) t -= cin[v][d] * xsol[d];
+          xsol[v] = t / dg[v];
+          st_relaxed(xvec + r0 + v, xsol[v]);
+        }
+      } else {
+#pragma unroll
+        for (int v = W - 1; v >= 0; v--) {
+          if (!act[v]) continue;
+          T t = acc[v];
+#pragma unroll
+          for (int d = 0; d < W; d++)
+            if (d > v) t -= cin[v][d] * xsol[d];
+          xsol[v] = t / dg[v];
+          st_relaxed(xvec + r0 + v, xsol[v]);
+        }
+      }
+    }
+    if (rounds > 1) __syncwarp();
+  }
+}
+
+}  // namespace nle

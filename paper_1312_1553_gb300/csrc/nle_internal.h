@@ -1,0 +1,112 @@
+// Internal data structures of the nle library (host setup + CUDA kernels).
+//
+// Layout in HBM
+//   Every device vector and matrix is stored in the LEVEL ORDER of the IC
+//   factor L: position i holds original row perm[i], where perm lists the
+//   rows level by level (ascending row inside a level).  Relabelling the
+//   unknowns changes no arithmetic of the method (dot products are
+//   permutation invariant and P L P^T is still triangular because a row only
+//   depends on rows of lower level), but it makes every level a contiguous
+//   range, so the triangular solves read and write vectors with unit stride.
+//   Vectors are padded to npad (a multiple of the slice height) with zeros.
+//
+//   Sparse matrices use a sliced-ELL format ("SELL") with slice height
+//   H = 32 * VW rows, where VW = 16 / sizeof(T) consecutive rows belong to one
+//   thread: a warp owns one slice, a lane owns VW adjacent rows and loads
+//   their e-th entries with one 16-byte load (val[base + e*H + lane*VW + v]).
+//   Padding entries carry value 0 and column = the row itself (SpMV) or the
+//   always-ready slot npad (triangular solves).
+#pragma once
+#include <cstdint>
+
+namespace nle {
+
+constexpr int TPB = 512;         // threads per CTA of the persistent kernels
+constexpr int NWARP = TPB / 32;  // warps per CTA
+constexpr int KMAX = 10;         // largest k_max
+constexpr int MMAX = 64;         // largest p (columns of Q)
+constexpr int RED_MAX = 160;     // reduction slots per pass
+
+template <typename T>
+struct Sell {
+  int64_t nslices = 0;
+  const int64_t *sptr = nullptr;  // nslices+1 offsets (elements)
+  const int32_t *col = nullptr;
+  const T *val = nullptr;
+};
+
+// Persistent solver state in device memory.  Written by CTA 0 only, at
+// points separated from every reader by a grid barrier or a kernel boundary.
+struct State {
+  int j;                 // eigenpair being computed (0-based)
+  int k;                 // number of stored BFGS pairs
+  int order[KMAX];       // chronological pair index -> physical slot
+  double alpha[KMAX];    // s^T r of each stored pair (chronological)
+  double theta;          // current Rayleigh quotient
+  double rnorm;          // ||A u - theta u||
+  int newton_its;
+  // per eigenpair results
+  double lambda[MMAX];
+  double res[MMAX];
+  int dacg_its[MMAX];
+  int outer_its[MMAX];
+  int pcg_its[MMAX];
+  int conv[MMAX];
+  long long mvp_dacg;
+  long long mvp_newton;
+  long long pcg_total;
+  long long pcg_sum_m;   // sum over inner iterations of the columns of Q
+  long long pcg_sum_k;   // sum over inner iterations of the stored pairs
+  long long dacg_sum_m;  // sum over DACG iterations of the deflated columns
+  long long dacg_total;  // DACG iterations
+  int exits[5];
+  // last single inner solve (nle_pcg)
+  int last_its, last_exit;
+  double last_g0, last_gn, last_eres;
+  // error word (0 = ok, else nle_status) and where a wait gave up
+  int err;
+  int err_where;
+  unsigned bar;  // grid barrier counter
+};
+
+struct Opts {
+  double tol;
+  double tau_pcg;
+  double tau_dacg;
+  int max_newton;
+  int max_pcg;
+  int max_dacg;
+  int kmax;
+  int exit_eigres;
+  int exit_stag;
+  int recompute;
+  long long spin_ns;
+};
+
+// Pointers handed to the persistent kernels (by value).
+template <typename T>
+struct Dev {
+  int64_t n = 0;        // true size
+  int64_t npad = 0;     // padded size (multiple of 32*VW)
+  int64_t nchunks = 0;  // npad / VW
+  int ldq = 0;          // allocated columns of Q / Qt
+  Sell<T> A;            // A in working precision
+  Sell<double> A64;     // A in FP64 (same pattern and layout as A)
+  Sell<T> L;            // strictly lower part of L (level order)
+  Sell<T> U;            // strictly upper part of U = L^T (level order)
+  const T *diag = nullptr;  // diagonal of L
+  const uint8_t *sub = nullptr;   // level of each row minus the lowest level of its slice
+  const uint8_t *nsub = nullptr;  // number of levels in each slice
+  // working-precision vectors (npad; z and c0 have npad + 32*VW entries)
+  T *p, *y, *s, *g, *z, *c0, *rT, *x, *Ax, *Ap;
+  T *Q;        // npad * ldq, column c at Q + c*npad (converged v_1.. and u)
+  T *S, *R;    // npad * KMAX, BFGS pairs by physical slot
+  // FP64 vectors
+  double *u, *Au, *r, *t;
+  double *Qt;  // npad * ldq, FP64 converged eigenvectors
+  // reductions / control
+  double *part;  // 2 * RED_MAX * gridDim
+  State *st;
+};
+
+}  // namespace nle

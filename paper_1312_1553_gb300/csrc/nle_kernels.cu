@@ -1,0 +1,1035 @@
+// Persistent cooperative kernels of the DACG-Newton eigensolver.
+//
+// One launch runs a whole phase on the device: DACG for eigenpair j
+// (Section 4.1), the Newton iteration for eigenpair j with every inner PCG
+// solve (Section 4.3, Algorithm 3.2), or one of the building blocks exposed
+// for verification.  Passes over the vectors are separated by a bounded grid
+// barrier; scalars are reduced deterministically so that every CTA takes the
+// same control decisions without a host round trip.
+//
+// Algorithm 3.1 is applied in Gram form: with G_SR[s][t] = s_s^T r_t and
+// G_QS[c][t] = q_c^T s_t (computed once per Newton step from the stored,
+// rounded vectors), the two loops of Algorithm 3.1 reduce to k x k
+// recurrences on scalars,
+//   a_s = (s_s^T g - sum_{t>s} a_t G_SR[s][t]) / alpha_s,   w = g - R a,
+//   c0  = Phat_0 w = L^{-T} L^{-1} w,
+//   b_s = (r_s^T c0 - sum_{t<s} (a_t+b_t) G_SR[t][s]) / alpha_s,
+//   z   = Q^T c0 - G_QS (a+b),   c = c0 - S (a+b) - Q z,
+// which is algebraically identical to the paper's loop (same a_s, b_s, z)
+// but needs one pass over S and R per dot-product group instead of 2k.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+
+#include "nle_device.cuh"
+
+namespace nle {
+
+// ---------------------------------------------------------------------------
+// small helpers over the chunks owned by a thread
+// ---------------------------------------------------------------------------
+// out[i][v] += sgn * sum_c coef[c] * X_c[row]   (X column c at X + c*ld)
+template <typename T, int RPC>
+__device__ __forceinline__ void comb_add(const T *X, int64_t ld, int ncol, const double *coef, const int *slot,
+                                         const Dev<T> &D, T (&out)[RPC][VT<T>::W], double sgn) {
+  constexpr int W = VT<T>::W;
+  const int64_t tid = gtid(), TT = gthreads();
+  for (int c = 0; c < ncol; c++) {
+    const T cf = T(sgn * coef[c]);
+    const T *col = X + (int64_t)(slot ? slot[c] : c) * ld;
+#pragma unroll
+    for (int i = 0; i < RPC; i++) {
+      const int64_t ch = tid + i * TT;
+      if (ch < D.nchunks) {
+        T q[W];
+        ldc(col + ch * W, q);
+#pragma unroll
+        for (int v = 0; v < W; v++) out[i][v] += cf * q[v];
+      }
+    }
+  }
+}
+
+// slot base.. : sum over owned rows of X_c[row] * val[i][v], for each column
+template <typename T, int RPC>
+__device__ __forceinline__ void dots_put(Shared &sh, int slot0, const T *X, int64_t ld, int ncol, const int *slot,
+                                         const Dev<T> &D, const T (&val)[RPC][VT<T>::W], bool reverse) {
+  constexpr int W = VT<T>::W;
+  const int64_t tid = gtid(), TT = gthreads();
+  for (int c = 0; c < ncol; c++) {
+    const T *col = X + (int64_t)(slot ? slot[c] : c) * ld;
+    double acc = 0.0;
+#pragma unroll
+    for (int i = 0; i < RPC; i++) {
+      const int64_t k = tid + i * TT;
+      const int64_t ch = reverse ? D.nchunks - 1 - k : k;
+      if (k < D.nchunks) {
+        T q[W];
+        ldc(col + ch * W, q);
+#pragma unroll
+        for (int v = 0; v < W; v++) acc += double(q[v]) * double(val[i][v]);
+      }
+    }
+    red_put(sh, slot0 + c, acc);
+  }
+}
+
+template <typename T, int RPC>
+__device__ __forceinline__ double self_dot(const T (&a)[RPC][VT<T>::W], const T (&b)[RPC][VT<T>::W]) {
+  double acc = 0.0;
+#pragma unroll
+  for (int i = 0; i < RPC; i++)
+#pragma unroll
+    for (int v = 0; v < VT<T>::W; v++) acc += double(a[i][v]) * double(b[i][v]);
+  return acc;
+}
+
+// ---------------------------------------------------------------------------
+// Gram form of Algorithm 3.1: scalar recurrences (one thread, every CTA)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void coef_a(Shared &sh, int k) {
+  if (threadIdx.x == 0) {
+    for (int s = k - 1; s >= 0; s--) {
+      double t = sh.sg[s];
+      for (int u = s + 1; u < k; u++) t -= sh.a[u] * sh.gsr[s][u];
+      sh.a[s] = t / sh.alpha[s];
+    }
+  }
+  __syncthreads();
+}
+
+// rc[t] = r_t^T c0 (chronological), qc[c] = q_c^T c0
+__device__ __forceinline__ void coef_b(Shared &sh, int k, int m, const double *rc, const double *qc) {
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < k; s++) {
+      double t = rc[s];
+      for (int u = 0; u < s; u++) t -= sh.ab[u] * sh.gsr[u][s];
+      sh.b[s] = t / sh.alpha[s];
+      sh.ab[s] = sh.a[s] + sh.b[s];
+    }
+    for (int c = 0; c < m; c++) {
+      double t = qc[c];
+      for (int u = 0; u < k; u++) t -= sh.ab[u] * sh.gqs[c][u];
+      sh.zq[c] = t;
+    }
+  }
+  __syncthreads();
+}
+
+// Gram matrices of the stored pairs: gsr[s][t] = s_s^T r_t, gqs[c][t] = q_c^T s_t.
+template <typename T, int RPC>
+__device__ bool gram(const Dev<T> &D, Shared &sh, Ctl &ctl, int m, int k) {
+  constexpr int W = VT<T>::W;
+  if (k == 0) return true;
+  const int64_t tid = gtid(), TT = gthreads();
+  const int per_s = k + m;  // slots per pair
+  const int smax = RED_MAX / per_s;
+  for (int s0 = 0; s0 < k; s0 += smax) {
+    const int s1 = min(k, s0 + smax);
+    for (int s = s0; s < s1; s++) {
+      T sv[RPC][W];
+      const T *scol = D.S + (int64_t)sh.order[s] * D.npad;
+#pragma unroll
+      for (int i = 0; i < RPC; i++) {
+        const int64_t ch = tid + i * TT;
+        if (ch < D.nchunks)
+          ldc(scol + ch * W, sv[i]);
+        else
+#pragma unroll
+          for (int v = 0; v < W; v++) sv[i][v] = T(0);
+      }
+      dots_put<T, RPC>(sh, (s - s0) * per_s, D.R, D.npad, k, sh.order, D, sv, false);
+      dots_put<T, RPC>(sh, (s - s0) * per_s + k, D.Q, D.npad, m, nullptr, D, sv, false);
+    }
+    if (!reduce_all(D, sh, ctl, (s1 - s0) * per_s, 10)) return false;
+    if (threadIdx.x == 0)
+      for (int s = s0; s < s1; s++) {
+        for (int t = 0; t < k; t++) sh.gsr[s][t] = sh.sc[(s - s0) * per_s + t];
+        for (int c = 0; c < m; c++) sh.gqs[c][s] = sh.sc[(s - s0) * per_s + k + c];
+      }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int s = 0; s < k; s++) sh.alpha[s] = sh.gsr[s][s];
+  __syncthreads();
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// preconditioner tail: forward solve on w = g - R a, backward solve, the dot
+// products of Algorithm 3.1's forward loop and Gram-Schmidt, and the output
+// pass out = c0 - S(a+b) - Q z (+ beta * out, beta = gamma'/gamma_old when
+// use_beta).  On entry gv holds g for the owned chunks and z/c0 hold the
+// not-yet-computed marker.  *gamma_new receives gamma' = g^T c.
+// ---------------------------------------------------------------------------
+template <typename T, int RPC>
+__device__ bool precond_tail(const Dev<T> &D, Shared &sh, Ctl &ctl, int m, int k, const T (&gv)[RPC][VT<T>::W],
+                             T *out, double gamma_old, bool use_beta, double *gamma_new) {
+  constexpr int W = VT<T>::W;
+  const int64_t tid = gtid(), TT = gthreads();
+  // forward solve L z = w, w = g - R a
+  {
+    T w[RPC][W];
+#pragma unroll
+    for (int i = 0; i < RPC; i++)
+#pragma unroll
+      for (int v = 0; v < W; v++) w[i][v] = gv[i][v];
+    if (k > 0) comb_add<T, RPC>(D.R, D.npad, k, sh.a, sh.order, D, w, -1.0);
+#pragma unroll
+    for (int i = 0; i < RPC; i++) {
+      const int64_t ch = tid + i * TT;
+      if (ch < D.nchunks) {
+        T zs[W];
+        solve_chunk<true, T>(D.L, D.diag, D.sub, D.nsub, D.z, ch, w[i], zs, D.st, ctl.spin_ns);
+      }
+    }
+  }
+  if (!grid_sync(D.st, sh, ctl, 20)) return false;
+  // backward solve L^T c0 = z (mirrored ownership), then the dot products
+  T cv[RPC][W];
+  {
+#pragma unroll
+    for (int i = 0; i < RPC; i++) {
+      const int64_t kk = tid + i * TT;
+      if (kk < D.nchunks) {
+        const int64_t ch = D.nchunks - 1 - kk;
+        T zz[W];
+        ldc(D.z + ch * W, zz);
+        solve_chunk<false, T>(D.U, D.diag, D.sub, D.nsub, D.c0, ch, zz, cv[i], D.st, ctl.spin_ns);
+      } else {
+#pragma unroll
+        for (int v = 0; v < W; v++) cv[i][v] = T(0);
+      }
+    }
+    // slots: [0,k) r_t^T c0 ; k: g^T c0 ; [k+1, k+1+m) q_c^T c0
+    dots_put<T, RPC>(sh, 0, D.R, D.npad, k, sh.order, D, cv, true);
+    {
+      double acc = 0.0;
+#pragma unroll
+      for (int i = 0; i < RPC; i++) {
+        const int64_t kk = tid + i * TT;
+        if (kk < D.nchunks) {
+          const int64_t ch = D.nchunks - 1 - kk;
+          T gg[W];
+          ldc(D.g + ch * W, gg);
+#pragma unroll
+          for (int v = 0; v < W; v++) acc += double(gg[v]) * double(cv[i][v]);
+        }
+      }
+      red_put(sh, k, acc);
+    }
+    dots_put<T, RPC>(sh, k + 1, D.Q, D.npad, m, nullptr, D, cv, true);
+  }
+  if (!reduce_all(D, sh, ctl, k + 1 + m, 21)) return false;
+  const double gc0 = sh.sc[k];
+  coef_b(sh, k, m, sh.sc, sh.sc + k + 1);
+  // gamma' = g^T c = g^T c0 - (S^T g)(a+b)   (g is orthogonal to Q)
+  double gnew = gc0;
+  for (int s = 0; s < k; s++) gnew -= sh.sg[s] * sh.ab[s];
+  *gamma_new = gnew;
+  const double beta = use_beta ? gnew / gamma_old : 0.0;
+  // output pass (natural ownership): out = c0 - S ab - Q z + beta*out
+  {
+    T o[RPC][W];
+#pragma unroll
+    for (int i = 0; i < RPC; i++) {
+      const int64_t ch = tid + i * TT;
+      if (ch < D.nchunks) {
+        ldc(D.c0 + ch * W, o[i]);
+      } else {
+#pragma unroll
+        for (int v = 0; v < W; v++) o[i][v] = T(0);
+      }
+    }
+    if (k > 0) comb_add<T, RPC>(D.S, D.npad, k, sh.ab, sh.order, D, o, -1.0);
+    if (m > 0) comb_add<T, RPC>(D.Q, D.npad, m, sh.zq, nullptr, D, o, -1.0);
+#pragma unroll
+    for (int i = 0; i < RPC; i++) {
+      const int64_t ch = tid + i * TT;
+      if (ch < D.nchunks) {
+        if (use_beta) {
+          T po[W];
+          ldc(out + ch * W, po);
+#pragma unroll
+          for (int v = 0; v < W; v++) o[i][v] += T(beta) * po[v];
+        }
+        stv(out + ch * W, o[i]);
+      }
+    }
+  }
+  return grid_sync(D.st, sh, ctl, 22);
+}
+
+// ---------------------------------------------------------------------------
+// PCG on the correction equation (Section 4.3): J s = -r, s perp Q, with
+// J = (I-QQ^T)(A - theta I)(I-QQ^T) and P_k by Algorithm 3.1.
+// Inputs in device memory: rT (r in working precision), Q (m columns), the
+// k stored pairs (sh.order, S, R) and their Gram matrices (sh.gsr, sh.gqs,
+// sh.alpha).  Output: s.  The residual g is kept orthogonal to Q by
+// g <- g - alpha (y - Q (Q^T y)), which equals the update followed by the
+// projection of g when g is orthogonal to Q.
+// ---------------------------------------------------------------------------
+struct PcgOut {
+  int its;
+  int exit;
+  double rs;  // r^T s at exit (= alpha of the new pair)
+  double g0, gn, eres;
+};
+
+template <typename T, int RPC>
+__device__ bool pcg_solve(const Dev<T> &D, const Opts &O, Shared &sh, Ctl &ctl, int m, int k, double theta,
+                          int max_pcg, PcgOut &res) {
+  constexpr int W = VT<T>::W;
+  const int64_t tid = gtid(), TT = gthreads();
+  const T Tsent = sentinel<T>();
+  T gv[RPC][W];
+  // --- initial residual g = -(I - QQ^T) r, s = 0
+  {
+    T rv[RPC][W];
+#pragma unroll
+    for (int i = 0; i < RPC; i++) {
+      const int64_t ch = tid + i * TT;
+      if (ch < D.nchunks)
+        ldc(D.rT + ch * W, rv[i]);
+      else
+#pragma unroll
+        for (int v = 0; v < W; v++) rv[i][v] = T(0);
+    }
+    dots_put<T, RPC>(sh, 0, D.Q, D.npad, m, nullptr, D, rv, false);
+    if (!reduce_all(D, sh, ctl, m, 30)) return false;
+    for (int c = threadIdx.x; c < m; c += TPB) sh.qv[c] = -sh.sc[c];
+    __syncthreads();
+    comb_add<T, RPC>(D.Q, D.npad, m, sh.qv, nullptr, D, rv, 1.0);  // rv = r - Q Q^T r
+    T sent[W], zero[W];
+#pragma unroll
+    for (int v = 0; v < W; v++) sent[v] = Tsent, zero[v] = T(0);
+#pragma unroll
+    for (int i = 0; i < RPC; i++) {
+      const int64_t ch = tid + i * TT;
+#pragma unroll
+      for (int v = 0; v < W; v++) gv[i][v] = -rv[i][v];
+      if (ch < D.nchunks) {
+        stv(D.g + ch * W, gv[i]);
+        stv(D.s + ch * W, zero);
+        stv(D.z + ch * W, sent);
+        stv(D.c0 + ch * W, sent);
+      }
+    }
+    red_put(sh, 0, self_dot<T, RPC>(gv, gv));
+    dots_put<T, RPC>(sh, 1, D.S, D.npad, k, sh.order, D, gv, false);
+    if (!reduce_all(D, sh, ctl, 1 + k, 31)) return false;
+  }
+  const double g0 = sqrt(sh.sc[0]);
+  if (threadIdx.x == 0)
+    for (int s = 0; s < k; s++) sh.sg[s] = sh.sc[1 + s];
+  __syncthreads();
+  coef_a(sh, k);
+  double gamma;
+  if (!precond_tail<T, RPC>(D, sh, ctl, m, k, gv, D.p, 0.0, false, &gamma)) return false;
+
+  res.g0 = g0;
+  res.gn = g0;
+  res.eres = 0.0;
+  res.rs = 0.0;
+  res.exit = 1;  // NLE_EXIT_MAXIT
+  res.its = 0;
+  double gprev = g0, eprev = 0.0;
+  for (int l = 0; l < max_pcg; l++) {
+    // --- pass A: y = (A - theta I) p, delta = p^T y, Q^T y
+    T yv[RPC][W];
+    {
+      double pty = 0.0;
+#pragma unroll
+      for (int i = 0; i < RPC; i++) {
+        const int64_t ch = tid + i * TT;
+        if (ch < D.nchunks) {
+          T acc[W], pp[W];
+          sell_rows<W, T, T, T>(D.A, D.p, ch, acc);
+          ldc(D.p + ch * W, pp);
+#pragma unroll
+          for (int v = 0; v < W; v++) {
+            yv[i][v] = acc[v] - T(theta) * pp[v];
+            pty += double(pp[v]) * double(yv[i][v]);
+          }
+          stv(D.y + ch * W, yv[i]);
+        } else {
+#pragma unroll
+          for (int v = 0; v < W; v++) yv[i][v] = T(0);
+        }
+      }
+      red_put(sh, 0, pty);
+      dots_put<T, RPC>(sh, 1, D.Q, D.npad, m, nullptr, D, yv, false);
+      if (!reduce_all(D, sh, ctl, 1 + m, 32)) return false;
+    }
+    const double delta = sh.sc[0];
+    if (!(delta > 0.0)) {
+      res.exit = 4;  // NLE_EXIT_BREAKDOWN
+      res.its = l;
+      break;
+    }
+    res.its = l + 1;
+    const double alpha = gamma / delta;
+    // --- pass B: s += alpha p; g -= alpha (y - Q Q^T y); exit scalars; S^T g
+    {
+      for (int c = threadIdx.x; c < m; c += TPB) sh.qv[c] = -sh.sc[1 + c];
+      __syncthreads();
+      comb_add<T, RPC>(D.Q, D.npad, m, sh.qv, nullptr, D, yv, 1.0);  // yv = (I - QQ^T) y
+      double rs = 0.0, sg = 0.0, ss = 0.0;
+      T sent[W];
+#pragma unroll
+      for (int v = 0; v < W; v++) sent[v] = Tsent;
+#pragma unroll
+      for (int i = 0; i < RPC; i++) {
+        const int64_t ch = tid + i * TT;
+        if (ch < D.nchunks) {
+          T pp[W], sv[W], rr[W];
+          ldc(D.p + ch * W, pp);
+          ldc(D.s + ch * W, sv);
+          ldc(D.g + ch * W, gv[i]);
+          ldc(D.rT + ch * W, rr);
+#pragma unroll
+          for (int v = 0; v < W; v++) {
+            sv[v] += T(alpha) * pp[v];
+            gv[i][v] -= T(alpha) * yv[i][v];
+            rs += double(rr[v]) * double(sv[v]);
+            sg += double(sv[v]) * double(gv[i][v]);
+            ss += double(sv[v]) * double(sv[v]);
+          }
+          stv(D.s + ch * W, sv);
+          stv(D.g + ch * W, gv[i]);
+          stv(D.z + ch * W, sent);
+          stv(D.c0 + ch * W, sent);
+        } else {
+#pragma unroll
+          for (int v = 0; v < W; v++) gv[i][v] = T(0);
+        }
+      }
+      red_put(sh, 0, self_dot<T, RPC>(gv, gv));
+      red_put(sh, 1, rs);
+      red_put(sh, 2, sg);
+      red_put(sh, 3, ss);
+      dots_put<T, RPC>(sh, 4, D.S, D.npad, k, sh.order, D, gv, false);
+      if (!reduce_all(D, sh, ctl, 4 + k, 33)) return false;
+    }
+    const double gn = sqrt(sh.sc[0]);
+    const double rs = sh.sc[1], sg = sh.sc[2], ss = sh.sc[3];
+    // eq. "residual" without a product with A (see oracle/solver.py)
+    const double x2 = 1.0 + ss;
+    const double dth = (rs - sg) / x2;
+    const double e2 = gn * gn + rs * rs - dth * dth * x2;
+    const double eres = sqrt(fmax(e2, 0.0) / x2);
+    const double rho = theta + dth;
+    res.gn = gn;
+    res.eres = eres;
+    res.rs = rs;
+    if (gn <= O.tau_pcg * g0) {
+      res.exit = 0;
+      break;
+    }
+    if (O.exit_eigres && eres < O.tol * rho) {
+      res.exit = 2;
+      break;
+    }
+    if (O.exit_stag && l >= 1 && eres / eprev > gn / gprev) {
+      res.exit = 3;
+      break;
+    }
+    if (l + 1 == max_pcg) {
+      res.exit = 1;
+      break;
+    }
+    if (threadIdx.x == 0)
+      for (int s = 0; s < k; s++) sh.sg[s] = sh.sc[4 + s];
+    __syncthreads();
+    coef_a(sh, k);
+    double gnew;
+    if (!precond_tail<T, RPC>(D, sh, ctl, m, k, gv, D.p, gamma, true, &gnew)) return false;
+    gamma = gnew;
+    gprev = gn;
+    eprev = eres;
+  }
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// FP64 pieces of the outer step
+// ---------------------------------------------------------------------------
+
+// Au = A u (FP64), returns u^T A u and u^T u in sh.sc[0..1].  u = Qt column j.
+template <typename T, int RPC>
+__device__ bool fp64_rayleigh(const Dev<T> &D, Shared &sh, Ctl &ctl, const double *u) {
+  constexpr int W = VT<T>::W;
+  const int64_t tid = gtid(), TT = gthreads();
+  double uau = 0.0, uu = 0.0;
+#pragma unroll
+  for (int i = 0; i < RPC; i++) {
+    const int64_t ch = tid + i * TT;
+    if (ch < D.nchunks) {
+      double acc[W], uv[W];
+      sell_rows<W, double, double, double>(D.A64, u, ch, acc);
+      ldc(u + ch * W, uv);
+#pragma unroll
+      for (int v = 0; v < W; v++) {
+        uau += uv[v] * acc[v];
+        uu += uv[v] * uv[v];
+      }
+      stv(D.Au + ch * W, acc);
+    }
+  }
+  red_put(sh, 0, uau);
+  red_put(sh, 1, uu);
+  return reduce_all(D, sh, ctl, 2, 40);
+}
+
+// r = Au - theta u, ||r||^2 in sh.sc[0]; shadows rT and Q[:, j] = u.
+template <typename T, int RPC>
+__device__ bool fp64_residual(const Dev<T> &D, Shared &sh, Ctl &ctl, const double *u, double theta, int j) {
+  constexpr int W = VT<T>::W;
+  const int64_t tid = gtid(), TT = gthreads();
+  double rr = 0.0;
+  T *uq = D.Q + (int64_t)j * D.npad;
+#pragma unroll
+  for (int i = 0; i < RPC; i++) {
+    const int64_t ch = tid + i * TT;
+    if (ch < D.nchunks) {
+      double au[W], uv[W], rv[W];
+      ldc(D.Au + ch * W, au);
+      ldc(u + ch * W, uv);
+      T rt[W], ut[W];
+#pragma unroll
+      for (int v = 0; v < W; v++) {
+        rv[v] = au[v] - theta * uv[v];
+        rr += rv[v] * rv[v];
+        rt[v] = T(rv[v]);
+        ut[v] = T(uv[v]);
+      }
+      stv(D.r + ch * W, rv);
+      stv(D.rT + ch * W, rt);
+      stv(uq + ch * W, ut);
+    }
+  }
+  red_put(sh, 0, rr);
+  return reduce_all(D, sh, ctl, 1, 41);
+}
+
+template <typename T>
+__device__ void load_state(const Dev<T> &D, Shared &sh, Ctl &ctl, long long spin_ns) {
+  ctl.epoch = 0;
+  ctl.rbuf = 0;
+  ctl.spin_ns = spin_ns;
+  if (threadIdx.x == 0) {
+    sh.ok = 1;
+    for (int s = 0; s < KMAX; s++) sh.order[s] = D.st->order[s];
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// Kernel: Newton iteration for eigenpair j (Algorithm 3.2, inner loop)
+// ---------------------------------------------------------------------------
+template <typename T, int RPC>
+__global__ void __launch_bounds__(TPB, 1) k_newton(Dev<T> D, Opts O) {
+  constexpr int W = VT<T>::W;
+  __shared__ Shared sh;
+  Ctl ctl;
+  load_state(D, sh, ctl, O.spin_ns);
+  const int64_t tid = gtid(), TT = gthreads();
+  const int j = D.st->j;
+  const int m = j + 1;
+  double *u = D.Qt + (int64_t)j * D.npad;
+  int k = 0;  // pairs reset for every eigenpair
+  if (threadIdx.x == 0)
+    for (int s = 0; s < KMAX; s++) sh.order[s] = s;
+  __syncthreads();
+  long long mvp = 0, pcg_total = 0, sum_m = 0, sum_k = 0;
+  int pcg_sum = 0;
+  int exits[5] = {0, 0, 0, 0, 0};
+
+  if (!fp64_rayleigh<T, RPC>(D, sh, ctl, u)) return;
+  mvp++;
+  double theta = sh.sc[0] / sh.sc[1];
+  if (!fp64_residual<T, RPC>(D, sh, ctl, u, theta, j)) return;
+  double rnorm = sqrt(sh.sc[0]);
+  int it = 0;
+  while (rnorm > O.tol * theta && it < O.max_newton) {
+    if (!gram<T, RPC>(D, sh, ctl, m, k)) return;
+    PcgOut po;
+    if (!pcg_solve<T, RPC>(D, O, sh, ctl, m, k, theta, O.max_pcg, po)) return;
+    mvp += po.its;
+    pcg_total += po.its;
+    pcg_sum += po.its;
+    sum_m += (long long)po.its * m;
+    sum_k += (long long)po.its * k;
+    exits[po.exit]++;
+    // store the pair (s_k, r_k) when alpha < 0 (Theorem 3.2); ring of k_max
+    int slot = -1;
+    if (O.kmax > 0 && po.rs < 0.0) {
+      if (k < O.kmax) {
+        slot = k;
+        if (threadIdx.x == 0) sh.order[k] = k;
+        k++;
+      } else {
+        if (threadIdx.x == 0) {
+          slot = sh.order[0];
+          for (int s = 0; s + 1 < k; s++) sh.order[s] = sh.order[s + 1];
+          sh.order[k - 1] = slot;
+        }
+        __syncthreads();
+        slot = sh.order[k - 1];
+      }
+    }
+    __syncthreads();
+    // N1: t = u + s (FP64); copy the pair; ||t||^2, Qt^T t
+    double tv[RPC][W];
+    {
+      double tt = 0.0;
+#pragma unroll
+      for (int i = 0; i < RPC; i++) {
+        const int64_t ch = tid + i * TT;
+        if (ch < D.nchunks) {
+          double uv[W];
+          T sv[W];
+          ldc(u + ch * W, uv);
+          ldc(D.s + ch * W, sv);
+#pragma unroll
+          for (int v = 0; v < W; v++) {
+            tv[i][v] = uv[v] + double(sv[v]);
+            tt += tv[i][v] * tv[i][v];
+          }
+          if (slot >= 0) {
+            T rt[W];
+            ldc(D.rT + ch * W, rt);
+            stv(D.S + (int64_t)slot * D.npad + ch * W, sv);
+            stv(D.R + (int64_t)slot * D.npad + ch * W, rt);
+          }
+        } else {
+#pragma unroll
+          for (int v = 0; v < W; v++) tv[i][v] = 0.0;
+        }
+      }
+      red_put(sh, 0, tt);
+      for (int c = 0; c < j; c++) {
+        const double *qc = D.Qt + (int64_t)c * D.npad;
+        double acc = 0.0;
+#pragma unroll
+        for (int i = 0; i < RPC; i++) {
+          const int64_t ch = tid + i * TT;
+          if (ch < D.nchunks) {
+            double q[W];
+            ldc(qc + ch * W, q);
+#pragma unroll
+            for (int v = 0; v < W; v++) acc += q[v] * tv[i][v];
+          }
+        }
+        red_put(sh, 1 + c, acc);
+      }
+      if (!reduce_all(D, sh, ctl, 1 + j, 42)) return;
+    }
+    // N2: u = (t - Qt (Qt^T t)) / ||.||  (re-orthogonalisation against the
+    // converged eigenvectors, then normalisation)
+    {
+      double nq = 0.0;
+      for (int c = 0; c < j; c++) nq += sh.sc[1 + c] * sh.sc[1 + c];
+      const double inv = 1.0 / sqrt(sh.sc[0] - nq);
+      for (int c = 0; c < j; c++) {
+        const double *qc = D.Qt + (int64_t)c * D.npad;
+        const double cf = sh.sc[1 + c];
+#pragma unroll
+        for (int i = 0; i < RPC; i++) {
+          const int64_t ch = tid + i * TT;
+          if (ch < D.nchunks) {
+            double q[W];
+            ldc(qc + ch * W, q);
+#pragma unroll
+            for (int v = 0; v < W; v++) tv[i][v] -= cf * q[v];
+          }
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < RPC; i++) {
+        const int64_t ch = tid + i * TT;
+        if (ch < D.nchunks) {
+#pragma unroll
+          for (int v = 0; v < W; v++) tv[i][v] *= inv;
+          stv(u + ch * W, tv[i]);
+        }
+      }
+      if (!grid_sync(D.st, sh, ctl, 43)) return;
+    }
+    if (!fp64_rayleigh<T, RPC>(D, sh, ctl, u)) return;
+    mvp++;
+    theta = sh.sc[0] / sh.sc[1];
+    if (!fp64_residual<T, RPC>(D, sh, ctl, u, theta, j)) return;
+    rnorm = sqrt(sh.sc[0]);
+    it++;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    State *st = D.st;
+    st->theta = theta;
+    st->rnorm = rnorm;
+    st->lambda[j] = theta;
+    st->res[j] = rnorm / theta;
+    st->outer_its[j] = it;
+    st->pcg_its[j] = pcg_sum;
+    st->conv[j] = (rnorm <= O.tol * theta) ? 1 : 0;
+    st->mvp_newton += mvp;
+    st->pcg_total += pcg_total;
+    st->pcg_sum_m += sum_m;
+    st->pcg_sum_k += sum_k;
+    for (int e = 0; e < 5; e++) st->exits[e] += exits[e];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Kernel: DACG for eigenpair j (Section 4.1): preconditioned nonlinear CG on
+// the Rayleigh quotient in the complement of the converged eigenvectors.
+// On entry x holds the start vector; on exit Qt[:, j] holds u_0 (FP64).
+// ---------------------------------------------------------------------------
+template <typename T, int RPC>
+__global__ void __launch_bounds__(TPB, 1) k_dacg(Dev<T> D, Opts O) {
+  constexpr int W = VT<T>::W;
+  __shared__ Shared sh;
+  Ctl ctl;
+  load_state(D, sh, ctl, O.spin_ns);
+  const int64_t tid = gtid(), TT = gthreads();
+  const int j = D.st->j;
+  const int mq = j;  // converged eigenvectors (shadow columns of Q)
+  const T Tsent = sentinel<T>();
+  long long mvp = 0;
+  T xv[RPC][W];
+#pragma unroll
+  for (int i = 0; i < RPC; i++) {
+    const int64_t ch = tid + i * TT;
+    if (ch < D.nchunks)
+      ldc(D.x + ch * W, xv[i]);
+    else
+#pragma unroll
+      for (int v = 0; v < W; v++) xv[i][v] = T(0);
+  }
+  // x0 projected on the complement of Q~ twice (classical Gram-Schmidt)
+  for (int rep = 0; rep < 2 && mq > 0; rep++) {
+    dots_put<T, RPC>(sh, 0, D.Q, D.npad, mq, nullptr, D, xv, false);
+    if (!reduce_all(D, sh, ctl, mq, 50)) return;
+    for (int c = threadIdx.x; c < mq; c += TPB) sh.qv[c] = -sh.sc[c];
+    __syncthreads();
+    comb_add<T, RPC>(D.Q, D.npad, mq, sh.qv, nullptr, D, xv, 1.0);
+  }
+  red_put(sh, 0, self_dot<T, RPC>(xv, xv));
+  if (!reduce_all(D, sh, ctl, 1, 51)) return;
+  {
+    const T inv = T(1.0 / sqrt(sh.sc[0]));
+#pragma unroll
+    for (int i = 0; i < RPC; i++) {
+      const int64_t ch = tid + i * TT;
+#pragma unroll
+      for (int v = 0; v < W; v++) xv[i][v] *= inv;
+      if (ch < D.nchunks) stv(D.x + ch * W, xv[i]);
+    }
+  }
+  if (!grid_sync(D.st, sh, ctl, 52)) return;
+  // Ax
+#pragma unroll
+  for (int i = 0; i < RPC; i++) {
+    const int64_t ch = tid + i * TT;
+    if (ch < D.nchunks) {
+      T acc[W];
+      sell_rows<W, T, T, T>(D.A, D.x, ch, acc);
+      stv(D.Ax + ch * W, acc);
+    }
+  }
+  mvp++;
+  if (!grid_sync(D.st, sh, ctl, 53)) return;
+
+  double nx = 1.0, gg_prev = 0.0;
+  int its = 0;
+  for (int it = 0; it < O.max_dacg; it++) {
+    // P1: normalise x, Ax by the last norm; q = x^T A x, f = x^T x
+    T av[RPC][W];
+    {
+      const T inv = T(1.0 / nx);
+#pragma unroll
+      for (int i = 0; i < RPC; i++) {
+        const int64_t ch = tid + i * TT;
+        if (ch < D.nchunks) {
+          ldc(D.x + ch * W, xv[i]);
+          ldc(D.Ax + ch * W, av[i]);
+          if (nx != 1.0) {
+#pragma unroll
+            for (int v = 0; v < W; v++) xv[i][v] *= inv, av[i][v] *= inv;
+            stv(D.x + ch * W, xv[i]);
+            stv(D.Ax + ch * W, av[i]);
+          }
+        } else {
+#pragma unroll
+          for (int v = 0; v < W; v++) xv[i][v] = T(0), av[i][v] = T(0);
+        }
+      }
+      red_put(sh, 0, self_dot<T, RPC>(xv, av));
+      red_put(sh, 1, self_dot<T, RPC>(xv, xv));
+      if (!reduce_all(D, sh, ctl, 2, 54)) return;
+      nx = 1.0;  // x and Ax now hold the normalised iterate
+    }
+    const double q = sh.sc[0], f = sh.sc[1];
+    // P2: g = A x - q x, ||g||; reset the solve outputs
+    T gv[RPC][W];
+    {
+      T sent[W];
+#pragma unroll
+      for (int v = 0; v < W; v++) sent[v] = Tsent;
+#pragma unroll
+      for (int i = 0; i < RPC; i++) {
+        const int64_t ch = tid + i * TT;
+#pragma unroll
+        for (int v = 0; v < W; v++) gv[i][v] = av[i][v] - T(q) * xv[i][v];
+        if (ch < D.nchunks) {
+          stv(D.g + ch * W, gv[i]);
+          stv(D.z + ch * W, sent);
+          stv(D.c0 + ch * W, sent);
+        }
+      }
+      red_put(sh, 0, self_dot<T, RPC>(gv, gv));
+      if (!reduce_all(D, sh, ctl, 1, 55)) return;
+    }
+    if (sqrt(sh.sc[0]) <= O.tau_dacg * q) break;
+    // P3-P5: gt = (I - Q~Q~^T) Phat_0 g,  p = -gt + beta p
+    double gg;
+    {
+      // Phat_0 g via the preconditioner tail with no pairs, writing into Ap as
+      // scratch: Ap = c0 - Q z, then p = -Ap + beta p below.
+      if (!precond_tail<T, RPC>(D, sh, ctl, mq, 0, gv, D.Ap, 0.0, false, &gg)) return;
+      const double beta = (it == 0) ? 0.0 : gg / gg_prev;
+#pragma unroll
+      for (int i = 0; i < RPC; i++) {
+        const int64_t ch = tid + i * TT;
+        if (ch < D.nchunks) {
+          T gt[W], pp[W];
+          ldc(D.Ap + ch * W, gt);
+          if (it > 0) {
+            ldc(D.p + ch * W, pp);
+#pragma unroll
+            for (int v = 0; v < W; v++) pp[v] = -gt[v] + T(beta) * pp[v];
+          } else {
+#pragma unroll
+            for (int v = 0; v < W; v++) pp[v] = -gt[v];
+          }
+          stv(D.p + ch * W, pp);
+        }
+      }
+      if (!grid_sync(D.st, sh, ctl, 56)) return;
+    }
+    // P6: Ap = A p; line-search scalars
+    {
+      double a = 0.0, b = 0.0, d = 0.0, e = 0.0;
+#pragma unroll
+      for (int i = 0; i < RPC; i++) {
+        const int64_t ch = tid + i * TT;
+        if (ch < D.nchunks) {
+          T acc[W], pp[W];
+          sell_rows<W, T, T, T>(D.A, D.p, ch, acc);
+          ldc(D.p + ch * W, pp);
+#pragma unroll
+          for (int v = 0; v < W; v++) {
+            a += double(pp[v]) * double(acc[v]);
+            b += double(xv[i][v]) * double(acc[v]);
+            d += double(pp[v]) * double(pp[v]);
+            e += double(xv[i][v]) * double(pp[v]);
+          }
+          stv(D.Ap + ch * W, acc);
+        }
+      }
+      mvp++;
+      red_put(sh, 0, a);
+      red_put(sh, 1, b);
+      red_put(sh, 2, d);
+      red_put(sh, 3, e);
+      if (!reduce_all(D, sh, ctl, 4, 57)) return;
+    }
+    double al;
+    {
+      const double a = sh.sc[0], b = sh.sc[1], c = q, d = sh.sc[2], e = sh.sc[3];
+      const double A2 = a * e - b * d, B2 = a * f - c * d, C2 = b * f - c * e;
+      if (A2 == 0.0) {
+        al = (B2 != 0.0) ? -C2 / B2 : 0.0;
+      } else {
+        const double disc = fmax(B2 * B2 - 4.0 * A2 * C2, 0.0);
+        const double t = -0.5 * (B2 + copysign(sqrt(disc), B2));
+        const double r1 = t / A2;
+        al = r1;
+        if (t != 0.0) {
+          const double r2 = C2 / t;
+          const double q1 = (c + 2 * r1 * b + r1 * r1 * a) / (f + 2 * r1 * e + r1 * r1 * d);
+          const double q2 = (c + 2 * r2 * b + r2 * r2 * a) / (f + 2 * r2 * e + r2 * r2 * d);
+          if (q2 < q1) al = r2;
+        }
+      }
+    }
+    // P7: x += al p, Ax += al Ap, ||x||
+    {
+      double xx = 0.0;
+#pragma unroll
+      for (int i = 0; i < RPC; i++) {
+        const int64_t ch = tid + i * TT;
+        if (ch < D.nchunks) {
+          T pp[W], ap[W];
+          ldc(D.p + ch * W, pp);
+          ldc(D.Ap + ch * W, ap);
+#pragma unroll
+          for (int v = 0; v < W; v++) {
+            xv[i][v] += T(al) * pp[v];
+            av[i][v] += T(al) * ap[v];
+            xx += double(xv[i][v]) * double(xv[i][v]);
+          }
+          stv(D.x + ch * W, xv[i]);
+          stv(D.Ax + ch * W, av[i]);
+        }
+      }
+      red_put(sh, 0, xx);
+      if (!reduce_all(D, sh, ctl, 1, 58)) return;
+      nx = sqrt(sh.sc[0]);
+    }
+    its = it + 1;
+    if (O.recompute > 0 && its % O.recompute == 0) {
+#pragma unroll
+      for (int i = 0; i < RPC; i++) {
+        const int64_t ch = tid + i * TT;
+        if (ch < D.nchunks) {
+          T acc[W];
+          sell_rows<W, T, T, T>(D.A, D.x, ch, acc);
+          stv(D.Ax + ch * W, acc);
+        }
+      }
+      mvp++;
+      if (!grid_sync(D.st, sh, ctl, 59)) return;
+    }
+    gg_prev = gg;
+  }
+  // u_0 = x / ||x|| in FP64 into Qt[:, j]
+  {
+    double *u = D.Qt + (int64_t)j * D.npad;
+#pragma unroll
+    for (int i = 0; i < RPC; i++) {
+      const int64_t ch = tid + i * TT;
+      if (ch < D.nchunks) {
+        T xx[W];
+        ldc(D.x + ch * W, xx);
+        double uv[W];
+#pragma unroll
+        for (int v = 0; v < W; v++) uv[v] = double(xx[v]) / nx;
+        stv(u + ch * W, uv);
+      }
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    D.st->dacg_its[j] = its;
+    D.st->mvp_dacg += mvp;
+    D.st->dacg_total += its;
+    D.st->dacg_sum_m += (long long)its * mq;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Kernels exposing single building blocks (verification entry points)
+// ---------------------------------------------------------------------------
+
+// y = (A - theta I) x  (x in D.p, y in D.y)
+template <typename T, int RPC>
+__global__ void __launch_bounds__(TPB, 1) k_shifted(Dev<T> D, double theta) {
+  constexpr int W = VT<T>::W;
+  const int64_t tid = gtid(), TT = gthreads();
+#pragma unroll
+  for (int i = 0; i < RPC; i++) {
+    const int64_t ch = tid + i * TT;
+    if (ch < D.nchunks) {
+      T acc[W], pp[W];
+      sell_rows<W, T, T, T>(D.A, D.p, ch, acc);
+      ldc(D.p + ch * W, pp);
+#pragma unroll
+      for (int v = 0; v < W; v++) acc[v] -= T(theta) * pp[v];
+      stv(D.y + ch * W, acc);
+    }
+  }
+}
+
+// c = P_k g by Algorithm 3.1 (g in D.g, output in D.y); m columns of Q, k pairs
+// in slots 0..k-1 (chronological).
+template <typename T, int RPC>
+__global__ void __launch_bounds__(TPB, 1) k_prec(Dev<T> D, Opts O, int m, int k) {
+  constexpr int W = VT<T>::W;
+  __shared__ Shared sh;
+  Ctl ctl;
+  load_state(D, sh, ctl, O.spin_ns);
+  if (threadIdx.x == 0)
+    for (int s = 0; s < KMAX; s++) sh.order[s] = s;
+  __syncthreads();
+  if (!gram<T, RPC>(D, sh, ctl, m, k)) return;
+  const int64_t tid = gtid(), TT = gthreads();
+  const T Tsent = sentinel<T>();
+  T gv[RPC][W];
+  T sent[W];
+#pragma unroll
+  for (int v = 0; v < W; v++) sent[v] = Tsent;
+#pragma unroll
+  for (int i = 0; i < RPC; i++) {
+    const int64_t ch = tid + i * TT;
+    if (ch < D.nchunks) {
+      ldc(D.g + ch * W, gv[i]);
+      stv(D.z + ch * W, sent);
+      stv(D.c0 + ch * W, sent);
+    } else {
+#pragma unroll
+      for (int v = 0; v < W; v++) gv[i][v] = T(0);
+    }
+  }
+  dots_put<T, RPC>(sh, 0, D.S, D.npad, k, sh.order, D, gv, false);
+  if (!reduce_all(D, sh, ctl, k, 60)) return;
+  if (threadIdx.x == 0)
+    for (int s = 0; s < k; s++) sh.sg[s] = sh.sc[s];
+  __syncthreads();
+  coef_a(sh, k);
+  double gamma;
+  precond_tail<T, RPC>(D, sh, ctl, m, k, gv, D.y, 0.0, false, &gamma);
+}
+
+// One inner solve: theta given, r in rT, Q with m columns, k pairs in slots 0..k-1.
+template <typename T, int RPC>
+__global__ void __launch_bounds__(TPB, 1) k_pcg(Dev<T> D, Opts O, int m, int k, double theta, int max_pcg) {
+  __shared__ Shared sh;
+  Ctl ctl;
+  load_state(D, sh, ctl, O.spin_ns);
+  if (threadIdx.x == 0)
+    for (int s = 0; s < KMAX; s++) sh.order[s] = s;
+  __syncthreads();
+  if (!gram<T, RPC>(D, sh, ctl, m, k)) return;
+  PcgOut po;
+  if (!pcg_solve<T, RPC>(D, O, sh, ctl, m, k, theta, max_pcg, po)) return;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    D.st->last_its = po.its;
+    D.st->last_exit = po.exit;
+    D.st->last_g0 = po.g0;
+    D.st->last_gn = po.gn;
+    D.st->last_eres = po.eres;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host-side launch table.  This file is compiled once per (precision, RPC)
+// pair (NLE_T, NLE_RPC, NLE_TAG defined by the build) so that the
+// instantiations compile in parallel.
+// ---------------------------------------------------------------------------
+#if defined(NLE_T) && defined(NLE_RPC) && defined(NLE_TAG)
+#define NLE_CAT2(a, b) a##b
+#define NLE_CAT(a, b) NLE_CAT2(a, b)
+void *NLE_CAT(kernel_ptr_, NLE_TAG)(int id) {
+  switch (id) {
+    case 0: return (void *)k_newton<NLE_T, NLE_RPC>;
+    case 1: return (void *)k_dacg<NLE_T, NLE_RPC>;
+    case 2: return (void *)k_shifted<NLE_T, NLE_RPC>;
+    case 3: return (void *)k_prec<NLE_T, NLE_RPC>;
+    case 4: return (void *)k_pcg<NLE_T, NLE_RPC>;
+  }
+  return nullptr;
+}
+#endif
+
+}  // namespace nle

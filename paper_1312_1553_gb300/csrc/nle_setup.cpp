@@ -1,0 +1,367 @@
+// Host-side set-up of the nle library: CSR validation, the IC(lfil, tau_IC)
+// factor (Section 2), the level sets of L and L^T, the level-order
+// relabelling and the packing of the sliced-ELL matrices.
+//
+// The factor is the preconditioner Phat_0 = (L L^T)^{-1} of Section 2.  The
+// paper does not print the IC variant; the library uses a left-looking column
+// algorithm whose every floating-point operation happens in a fixed order
+// (stated in include/nle.h), so that its drop decisions are reproducible.
+// Implementation: columns of L are kept in compressed form; a "next entry"
+// cursor per finished column k points at its first row >= the column being
+// built, and per-row buckets list the columns whose cursor sits on that row
+// (so column j finds every k with L(j,k) != 0 without scanning).
+#include "nle_setup.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+namespace nle {
+
+int validate_csr(int64_t n, int64_t nnz, const int64_t *rp, const int32_t *ci, const double *va, std::string &msg) {
+  if (rp[0] != 0 || rp[n] != nnz) {
+    msg = "rowptr[0] must be 0 and rowptr[n] must equal nnz";
+    return 2;
+  }
+  std::vector<int64_t> cnt(n + 1, 0);
+  for (int64_t i = 0; i < n; i++) {
+    if (rp[i + 1] < rp[i]) {
+      msg = "rowptr is not monotone";
+      return 2;
+    }
+    bool diag = false;
+    for (int64_t e = rp[i]; e < rp[i + 1]; e++) {
+      const int64_t c = ci[e];
+      if (c < 0 || c >= n) {
+        msg = "column index out of range in row " + std::to_string(i);
+        return 2;
+      }
+      if (e > rp[i] && ci[e - 1] >= c) {
+        msg = "columns not strictly ascending in row " + std::to_string(i);
+        return 2;
+      }
+      if (c == i) {
+        diag = true;
+        if (!(va[e] > 0.0)) {
+          msg = "non-positive diagonal in row " + std::to_string(i);
+          return 3;
+        }
+      }
+      if (!std::isfinite(va[e])) {
+        msg = "non-finite value in row " + std::to_string(i);
+        return 2;
+      }
+      cnt[c + 1]++;
+    }
+    if (!diag) {
+      msg = "missing diagonal in row " + std::to_string(i);
+      return 2;
+    }
+  }
+  // symmetry: build the transpose and compare entry by entry
+  for (int64_t i = 0; i < n; i++) cnt[i + 1] += cnt[i];
+  std::vector<int64_t> fill(cnt.begin(), cnt.end() - 1);
+  std::vector<int32_t> tc(nnz);
+  std::vector<double> tv(nnz);
+  for (int64_t i = 0; i < n; i++)
+    for (int64_t e = rp[i]; e < rp[i + 1]; e++) {
+      const int64_t c = ci[e];
+      tc[fill[c]] = (int32_t)i;
+      tv[fill[c]] = va[e];
+      fill[c]++;
+    }
+  for (int64_t i = 0; i < n; i++) {
+    if (cnt[i + 1] - cnt[i] != rp[i + 1] - rp[i]) {
+      msg = "pattern is not symmetric (row " + std::to_string(i) + ")";
+      return 2;
+    }
+    for (int64_t e = rp[i], f = cnt[i]; e < rp[i + 1]; e++, f++) {
+      if (tc[f] != ci[e]) {
+        msg = "pattern is not symmetric (row " + std::to_string(i) + ")";
+        return 2;
+      }
+      const double a = va[e], b = tv[f];
+      if (std::fabs(a - b) > 1e-12 * std::max(std::fabs(a), std::fabs(b))) {
+        msg = "values are not symmetric (row " + std::to_string(i) + ")";
+        return 2;
+      }
+    }
+  }
+  return 0;
+}
+
+int ic_factor_host(int64_t n, const int64_t *rp, const int32_t *ci, const double *va, int lfil, double tau,
+                   Factor &F, int64_t *bad_col) {
+  // columns of L: colstart (n+1), rows / values appended column by column
+  std::vector<int64_t> cs(n + 1, 0);
+  std::vector<int32_t> rows;
+  std::vector<double> vals;
+  rows.reserve((size_t)n * (size_t)(std::min<int64_t>(lfil, n) + 1));
+  vals.reserve(rows.capacity());
+  std::vector<int64_t> cursor(n, -1);   // next entry of column k to apply
+  std::vector<int64_t> bhead(n, -1);    // bucket of row i: columns whose cursor row is i
+  std::vector<int64_t> bnext(n, -1);
+  std::vector<double> w(n, 0.0);
+  std::vector<int64_t> mark(n, -1);
+  std::vector<int64_t> touched;
+  std::vector<int64_t> ks;
+  struct Cand {
+    int64_t i;
+    double v, a;
+  };
+  std::vector<Cand> cand;
+  auto push_bucket = [&](int64_t k) {
+    const int64_t r = rows[cursor[k]];
+    bnext[k] = bhead[r];
+    bhead[r] = k;
+  };
+  for (int64_t j = 0; j < n; j++) {
+    touched.clear();
+    // column j of A from row j (symmetric storage), and ||A(:,j)||_2 summed
+    // over the whole row in ascending column order
+    double nrm2 = 0.0;
+    for (int64_t e = rp[j]; e < rp[j + 1]; e++) {
+      const double a = va[e];
+      nrm2 += a * a;
+      const int64_t i = ci[e];
+      if (i >= j) {
+        if (mark[i] != j) {
+          mark[i] = j;
+          touched.push_back(i);
+          w[i] = 0.0;
+        }
+        w[i] += a;
+      }
+    }
+    const double anorm = std::sqrt(nrm2);
+    // columns k < j with L(j,k) != 0, in ascending k
+    ks.clear();
+    for (int64_t k = bhead[j]; k >= 0; k = bnext[k]) ks.push_back(k);
+    bhead[j] = -1;
+    std::sort(ks.begin(), ks.end());
+    for (int64_t k : ks) {
+      const int64_t e0 = cursor[k];
+      const double ljk = vals[e0];
+      for (int64_t e = e0; e < cs[k + 1]; e++) {
+        const int64_t i = rows[e];
+        if (mark[i] != j) {
+          mark[i] = j;
+          touched.push_back(i);
+          w[i] = 0.0;
+        }
+        w[i] -= vals[e] * ljk;
+      }
+      cursor[k] = e0 + 1;
+      if (cursor[k] < cs[k + 1]) push_bucket(k);
+    }
+    const double d = w[j];
+    if (!(d > 0.0)) {
+      if (bad_col) *bad_col = j;
+      return -2;
+    }
+    const double ljj = std::sqrt(d);
+    cand.clear();
+    for (int64_t i : touched) {
+      if (i == j) continue;
+      const double lij = w[i] / ljj;
+      if (!(std::fabs(lij) < tau * anorm)) cand.push_back({i, lij, std::fabs(lij)});
+    }
+    if ((int64_t)cand.size() > lfil) {
+      auto bigger = [](const Cand &x, const Cand &y) { return x.a > y.a || (x.a == y.a && x.i < y.i); };
+      std::nth_element(cand.begin(), cand.begin() + lfil, cand.end(), bigger);
+      cand.resize(lfil);
+    }
+    std::sort(cand.begin(), cand.end(), [](const Cand &x, const Cand &y) { return x.i < y.i; });
+    rows.push_back((int32_t)j);
+    vals.push_back(ljj);
+    for (const Cand &c : cand) {
+      rows.push_back((int32_t)c.i);
+      vals.push_back(c.v);
+    }
+    cs[j + 1] = (int64_t)rows.size();
+    if (!cand.empty()) {
+      cursor[j] = cs[j] + 1;
+      push_bucket(j);
+    }
+  }
+  // L by rows (diagonal last), from the columns
+  const int64_t nnz = (int64_t)rows.size();
+  F.n = n;
+  F.Lrowptr.assign(n + 1, 0);
+  for (int64_t e = 0; e < nnz; e++) F.Lrowptr[rows[e] + 1]++;
+  for (int64_t i = 0; i < n; i++) F.Lrowptr[i + 1] += F.Lrowptr[i];
+  F.Lcol.resize(nnz);
+  F.Lval.resize(nnz);
+  std::vector<int64_t> fill(F.Lrowptr.begin(), F.Lrowptr.end() - 1);
+  for (int64_t k = 0; k < n; k++)
+    for (int64_t e = cs[k]; e < cs[k + 1]; e++) {
+      const int64_t i = rows[e];
+      F.Lcol[fill[i]] = (int32_t)k;
+      F.Lval[fill[i]] = vals[e];
+      fill[i]++;
+    }
+  F.Ccolptr = std::move(cs);
+  F.Crow = std::move(rows);
+  F.Cval = std::move(vals);
+  // levels: L by pushing along columns (ascending), U = L^T by pulling
+  // along columns (descending)
+  F.levL.assign(n, 0);
+  F.levU.assign(n, 0);
+  for (int64_t k = 0; k < n; k++)
+    for (int64_t e = F.Ccolptr[k] + 1; e < F.Ccolptr[k + 1]; e++) {
+      const int64_t i = F.Crow[e];
+      F.levL[i] = std::max(F.levL[i], F.levL[k] + 1);
+    }
+  for (int64_t k = n - 1; k >= 0; k--) {
+    int32_t l = 0;
+    for (int64_t e = F.Ccolptr[k] + 1; e < F.Ccolptr[k + 1]; e++) l = std::max(l, F.levU[F.Crow[e]] + 1);
+    F.levU[k] = l;
+  }
+  F.nlevL = 0;
+  F.nlevU = 0;
+  for (int64_t i = 0; i < n; i++) {
+    F.nlevL = std::max<int64_t>(F.nlevL, F.levL[i] + 1);
+    F.nlevU = std::max<int64_t>(F.nlevU, F.levU[i] + 1);
+  }
+  return 0;
+}
+
+void level_order(const Factor &F, std::vector<int32_t> &perm, std::vector<int32_t> &iperm) {
+  const int64_t n = F.n;
+  std::vector<int64_t> ptr(F.nlevL + 1, 0);
+  for (int64_t i = 0; i < n; i++) ptr[F.levL[i] + 1]++;
+  for (int64_t l = 0; l < F.nlevL; l++) ptr[l + 1] += ptr[l];
+  perm.assign(n, 0);
+  iperm.assign(n, 0);
+  for (int64_t i = 0; i < n; i++) {
+    const int64_t p = ptr[F.levL[i]]++;
+    perm[p] = (int32_t)i;
+    iperm[i] = (int32_t)p;
+  }
+}
+
+// Pack rows of a matrix given row by row (in new numbering) into SELL.
+template <typename TV>
+static void pack(int64_t n, int64_t npad, int H, const std::vector<int64_t> &rp, const std::vector<int32_t> &col,
+                 const std::vector<double> &val, int pad_mode, int64_t pad_col, SellHost<TV> &out) {
+  const int64_t ns = npad / H;
+  out.nslices = ns;
+  out.sptr.assign(ns + 1, 0);
+  for (int64_t s = 0; s < ns; s++) {
+    int64_t w = 0;
+    for (int64_t r = s * H; r < std::min(n, (s + 1) * H); r++) w = std::max(w, rp[r + 1] - rp[r]);
+    out.sptr[s + 1] = out.sptr[s] + w * H;
+  }
+  out.col.assign(out.sptr[ns], 0);
+  out.val.assign(out.sptr[ns], TV(0));
+  for (int64_t s = 0; s < ns; s++) {
+    const int64_t base = out.sptr[s];
+    const int64_t w = (out.sptr[s + 1] - base) / H;
+    for (int64_t q = 0; q < H; q++) {
+      const int64_t r = s * H + q;
+      const int64_t len = (r < n) ? rp[r + 1] - rp[r] : 0;
+      for (int64_t e = 0; e < w; e++) {
+        const int64_t idx = base + e * H + q;
+        if (e < len) {
+          out.col[idx] = col[rp[r] + e];
+          out.val[idx] = TV(val[rp[r] + e]);
+        } else {
+          out.col[idx] = (int32_t)(pad_mode == 0 ? r : pad_col);
+          out.val[idx] = TV(0);
+        }
+      }
+    }
+  }
+}
+
+template <typename TV>
+void build_sell(const Permuted &P, int H, SellSet<TV> &S) {
+  pack<TV>(P.n, P.npad, H, P.Arp, P.Acol, P.Aval, 0, 0, S.A);
+  pack<double>(P.n, P.npad, H, P.Arp, P.Acol, P.Aval, 0, 0, S.A64);
+  pack<TV>(P.n, P.npad, H, P.Lrp, P.Lcol, P.Lval, 1, P.npad, S.L);
+  pack<TV>(P.n, P.npad, H, P.Urp, P.Ucol, P.Uval, 1, P.npad, S.U);
+  S.diag.assign(P.npad, TV(1));
+  for (int64_t i = 0; i < P.n; i++) S.diag[i] = TV(P.diag[i]);
+  // rounds of the triangular solves: levels are contiguous in the relabelled
+  // order, so a slice of H rows spans levels lev[first] .. lev[last] (<= H)
+  const int64_t ns = P.npad / H;
+  S.sub.assign(P.npad, 0);
+  S.nsub.assign(ns, 1);
+  for (int64_t s = 0; s < ns; s++) {
+    const int64_t r0 = s * H;
+    if (r0 >= P.n) continue;
+    const int32_t l0 = P.lev[r0];
+    int32_t top = 0;
+    for (int64_t r = r0; r < std::min(P.n, r0 + H); r++) {
+      S.sub[r] = (uint8_t)(P.lev[r] - l0);
+      top = std::max(top, P.lev[r] - l0);
+    }
+    S.nsub[s] = (uint8_t)(top + 1);
+  }
+}
+
+template void build_sell<float>(const Permuted &, int, SellSet<float> &);
+template void build_sell<double>(const Permuted &, int, SellSet<double> &);
+
+void permute(int64_t n, const int64_t *rp, const int32_t *ci, const double *va, const Factor &F,
+             const std::vector<int32_t> &perm, const std::vector<int32_t> &iperm, int64_t npad, Permuted &P) {
+  P.n = n;
+  P.npad = npad;
+  P.lev.assign(n, 0);
+  for (int64_t i = 0; i < n; i++) P.lev[i] = F.levL[perm[i]];
+  // A' = P A P^T, rows sorted by new column
+  std::vector<std::pair<int32_t, double>> tmp;
+  P.Arp.assign(n + 1, 0);
+  P.Acol.clear();
+  P.Aval.clear();
+  P.Acol.reserve(rp[n]);
+  P.Aval.reserve(rp[n]);
+  for (int64_t i = 0; i < n; i++) {
+    const int64_t o = perm[i];
+    tmp.clear();
+    for (int64_t e = rp[o]; e < rp[o + 1]; e++) tmp.push_back({iperm[ci[e]], va[e]});
+    std::sort(tmp.begin(), tmp.end(), [](auto &a, auto &b) { return a.first < b.first; });
+    for (auto &t : tmp) {
+      P.Acol.push_back(t.first);
+      P.Aval.push_back(t.second);
+    }
+    P.Arp[i + 1] = (int64_t)P.Acol.size();
+  }
+  // strictly lower part of L' and strictly upper part of U' = L'^T, diagonal
+  P.diag.assign(n, 0.0);
+  P.Lrp.assign(n + 1, 0);
+  P.Lcol.clear();
+  P.Lval.clear();
+  for (int64_t i = 0; i < n; i++) {
+    const int64_t o = perm[i];
+    tmp.clear();
+    for (int64_t e = F.Lrowptr[o]; e < F.Lrowptr[o + 1]; e++) {
+      if (F.Lcol[e] == o)
+        P.diag[i] = F.Lval[e];
+      else
+        tmp.push_back({iperm[F.Lcol[e]], F.Lval[e]});
+    }
+    std::sort(tmp.begin(), tmp.end(), [](auto &a, auto &b) { return a.first < b.first; });
+    for (auto &t : tmp) {
+      P.Lcol.push_back(t.first);
+      P.Lval.push_back(t.second);
+    }
+    P.Lrp[i + 1] = (int64_t)P.Lcol.size();
+  }
+  P.Urp.assign(n + 1, 0);
+  P.Ucol.clear();
+  P.Uval.clear();
+  for (int64_t i = 0; i < n; i++) {
+    const int64_t o = perm[i];  // row i of U' = column o of L
+    tmp.clear();
+    for (int64_t e = F.Ccolptr[o] + 1; e < F.Ccolptr[o + 1]; e++) tmp.push_back({iperm[F.Crow[e]], F.Cval[e]});
+    std::sort(tmp.begin(), tmp.end(), [](auto &a, auto &b) { return a.first < b.first; });
+    for (auto &t : tmp) {
+      P.Ucol.push_back(t.first);
+      P.Uval.push_back(t.second);
+    }
+    P.Urp[i + 1] = (int64_t)P.Ucol.size();
+  }
+}
+
+}  // namespace nle

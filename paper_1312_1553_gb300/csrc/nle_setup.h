@@ -1,0 +1,66 @@
+// Host-side set-up of the nle library (see nle_setup.cpp).
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace nle {
+
+struct Factor {
+  int64_t n = 0;
+  // L by rows, diagonal last (exported by nle_get_factor)
+  std::vector<int64_t> Lrowptr;
+  std::vector<int32_t> Lcol;
+  std::vector<double> Lval;
+  // L by columns, diagonal first (= U = L^T by rows)
+  std::vector<int64_t> Ccolptr;
+  std::vector<int32_t> Crow;
+  std::vector<double> Cval;
+  std::vector<int32_t> levL, levU;
+  int64_t nlevL = 0, nlevU = 0;
+};
+
+// Relabelled (level-order) matrices, row by row.
+struct Permuted {
+  int64_t n = 0, npad = 0;
+  std::vector<int64_t> Arp, Lrp, Urp;
+  std::vector<int32_t> Acol, Lcol, Ucol;
+  std::vector<double> Aval, Lval, Uval, diag;
+  std::vector<int32_t> lev;  // level (of L) of every relabelled row
+};
+
+template <typename TV>
+struct SellHost {
+  int64_t nslices = 0;
+  std::vector<int64_t> sptr;
+  std::vector<int32_t> col;
+  std::vector<TV> val;
+};
+
+template <typename TV>
+struct SellSet {
+  SellHost<TV> A, L, U;
+  SellHost<double> A64;
+  std::vector<TV> diag;
+  std::vector<uint8_t> sub;   // per row: level minus the lowest level of its slice
+  std::vector<uint8_t> nsub;  // per slice: number of levels it spans
+};
+
+// 0 on success; 2 = malformed CSR, 3 = non-positive diagonal (msg says why).
+int validate_csr(int64_t n, int64_t nnz, const int64_t *rp, const int32_t *ci, const double *va, std::string &msg);
+
+// IC(lfil, tau) of A plus the levels of L and L^T.  0 on success, -2 on a
+// non-positive pivot (column in *bad_col).
+int ic_factor_host(int64_t n, const int64_t *rp, const int32_t *ci, const double *va, int lfil, double tau,
+                   Factor &F, int64_t *bad_col);
+
+// perm[new] = old: rows level by level (ascending row inside a level).
+void level_order(const Factor &F, std::vector<int32_t> &perm, std::vector<int32_t> &iperm);
+
+void permute(int64_t n, const int64_t *rp, const int32_t *ci, const double *va, const Factor &F,
+             const std::vector<int32_t> &perm, const std::vector<int32_t> &iperm, int64_t npad, Permuted &P);
+
+template <typename TV>
+void build_sell(const Permuted &P, int H, SellSet<TV> &S);
+
+}  // namespace nle

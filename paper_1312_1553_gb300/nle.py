@@ -1,0 +1,289 @@
+"""Thin Python binding of the nle C ABI (include/nle.h).
+
+The functions below carry the C names and only marshal arguments (ctypes);
+every step of the method runs in the CUDA library.  ``Eigensolver`` wraps a
+handle with torch tensors: PyTorch supplies device memory and the stream.
+Loading fails loudly when the library has not been built; there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libnle.so")
+
+NLE_OK = 0
+STATUS = {0: "NLE_OK", 1: "NLE_ERR_ARG", 2: "NLE_ERR_CSR", 3: "NLE_ERR_NOT_SPD", 4: "NLE_ERR_BREAKDOWN",
+          5: "NLE_ERR_NOCONV", 6: "NLE_ERR_CUDA", 7: "NLE_ERR_OOM", 8: "NLE_ERR_TIMEOUT", 9: "NLE_ERR_STATE",
+          10: "NLE_ERR_NO_DEVICE"}
+NLE_FP64, NLE_MIXED = 0, 1
+EXITS = ("tol", "maxit", "eigres", "stagnation", "breakdown")
+NLE_MAX_P = 64
+
+# every symbol include/nle.h declares
+EXPORTS = ("nle_default_options", "nle_create", "nle_factor_ic", "nle_solve", "nle_backward", "nle_batch_solve",
+           "nle_apply_shifted", "nle_apply_prec", "nle_pcg", "nle_get_factor", "nle_last_error", "nle_destroy")
+
+
+class nle_options(ctypes.Structure):
+    _fields_ = [("k_max", ctypes.c_int), ("tau_pcg", ctypes.c_double), ("tau_dacg", ctypes.c_double),
+                ("max_dacg", ctypes.c_int), ("precision", ctypes.c_int), ("exit_eigres", ctypes.c_int),
+                ("exit_stagnation", ctypes.c_int), ("dacg_recompute", ctypes.c_int),
+                ("spin_timeout_s", ctypes.c_double), ("grid_ctas", ctypes.c_int)]
+
+
+class nle_stats(ctypes.Structure):
+    _fields_ = [("p", ctypes.c_int), ("dacg_its", ctypes.c_int * NLE_MAX_P), ("outer_its", ctypes.c_int * NLE_MAX_P),
+                ("pcg_its", ctypes.c_int * NLE_MAX_P), ("converged", ctypes.c_int * NLE_MAX_P),
+                ("final_res", ctypes.c_double * NLE_MAX_P), ("mvp_dacg", ctypes.c_int64),
+                ("mvp_newton", ctypes.c_int64), ("exit_count", ctypes.c_int * 5), ("ms_dacg", ctypes.c_double),
+                ("ms_newton", ctypes.c_double), ("ms_pcg_inner", ctypes.c_double),
+                ("pcg_iterations", ctypes.c_int64), ("pcg_sum_m", ctypes.c_int64), ("pcg_sum_k", ctypes.c_int64),
+                ("dacg_iterations", ctypes.c_int64), ("dacg_sum_m", ctypes.c_int64),
+                ("kernel_launches", ctypes.c_int64), ("ascending", ctypes.c_int)]
+
+
+class nle_pcg_info(ctypes.Structure):
+    _fields_ = [("its", ctypes.c_int), ("exit", ctypes.c_int), ("gnorm0", ctypes.c_double),
+                ("gnorm", ctypes.c_double), ("eigres", ctypes.c_double)]
+
+
+_vp = ctypes.c_void_p
+_i64 = ctypes.c_int64
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libnle.so (raises if it is missing: build it with __graft_entry__.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"nle CUDA library not built: {path} is missing")
+    lib = ctypes.CDLL(path)
+    sig = {
+        "nle_default_options": (None, [ctypes.POINTER(nle_options)]),
+        "nle_create": (ctypes.c_int, [_i64, _i64, _vp, _vp, _vp, ctypes.c_int, _vp, ctypes.POINTER(nle_options),
+                                      ctypes.POINTER(_vp)]),
+        "nle_factor_ic": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_double]),
+        "nle_solve": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp,
+                                     ctypes.POINTER(nle_stats), ctypes.c_int]),
+        "nle_backward": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_int]),
+        "nle_batch_solve": (ctypes.c_int, [ctypes.c_int, _vp, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                           ctypes.c_int, _vp, _vp, _vp, _vp]),
+        "nle_apply_shifted": (ctypes.c_int, [_vp, ctypes.c_double, _vp, _vp, ctypes.c_int]),
+        "nle_apply_prec": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, ctypes.c_int, _vp, _vp, _vp, ctypes.c_int]),
+        "nle_pcg": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_double, ctypes.c_int, _vp, ctypes.c_int, _vp,
+                                   ctypes.c_int, _vp, _vp, _vp, ctypes.POINTER(nle_pcg_info), ctypes.c_int]),
+        "nle_get_factor": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+        "nle_last_error": (ctypes.c_char_p, [_vp]),
+        "nle_destroy": (None, [_vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+class NLEError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+# ---- functions with the C names (argument marshalling only) ---------------
+
+def nle_default_options() -> nle_options:
+    o = nle_options()
+    load_library().nle_default_options(ctypes.byref(o))
+    return o
+
+
+def nle_last_error(h) -> str:
+    m = load_library().nle_last_error(h)
+    return m.decode() if m else ""
+
+
+def nle_create(n, nnz, rowptr_ptr, col_ptr, val_ptr, on_device, stream_ptr, opt: Optional[nle_options]):
+    out = _vp()
+    st = load_library().nle_create(n, nnz, rowptr_ptr, col_ptr, val_ptr, int(on_device), stream_ptr,
+                                   ctypes.byref(opt) if opt is not None else None, ctypes.byref(out))
+    return st, out
+
+
+def nle_factor_ic(h, lfil: int, tau_ic: float) -> int:
+    return load_library().nle_factor_ic(h, int(lfil), float(tau_ic))
+
+
+def nle_solve(h, p, tol, max_newton, max_pcg, X0_ptr, lambda_ptr, V_ptr, stats: Optional[nle_stats], on_device):
+    return load_library().nle_solve(h, int(p), float(tol), int(max_newton), int(max_pcg), X0_ptr, lambda_ptr, V_ptr,
+                                    ctypes.byref(stats) if stats is not None else None, int(on_device))
+
+
+def nle_backward(h, gl_ptr, gv_ptr, grad_ptr, on_device) -> int:
+    return load_library().nle_backward(h, gl_ptr, gv_ptr, grad_ptr, int(on_device))
+
+
+def nle_batch_solve(count, handles_ptr, p, tol, max_newton, max_pcg, x0s_ptr, lambdas_ptr, vs_ptr, per_ptr) -> int:
+    return load_library().nle_batch_solve(int(count), handles_ptr, int(p), float(tol), int(max_newton),
+                                          int(max_pcg), x0s_ptr, lambdas_ptr, vs_ptr, per_ptr)
+
+
+def nle_apply_shifted(h, theta, x_ptr, y_ptr, on_device) -> int:
+    return load_library().nle_apply_shifted(h, float(theta), x_ptr, y_ptr, int(on_device))
+
+
+def nle_apply_prec(h, k, S_ptr, R_ptr, m, Q_ptr, g_ptr, c_ptr, on_device) -> int:
+    return load_library().nle_apply_prec(h, int(k), S_ptr, R_ptr, int(m), Q_ptr, g_ptr, c_ptr, int(on_device))
+
+
+def nle_pcg(h, theta, tol, max_pcg, r_ptr, m, Q_ptr, k, S_ptr, R_ptr, s_ptr, info: nle_pcg_info, on_device) -> int:
+    return load_library().nle_pcg(h, float(theta), float(tol), int(max_pcg), r_ptr, int(m), Q_ptr, int(k), S_ptr,
+                                  R_ptr, s_ptr, ctypes.byref(info), int(on_device))
+
+
+def nle_get_factor(h, nnz_ptr, rp_ptr, col_ptr, val_ptr, levL_ptr, levU_ptr, nlevL_ptr, nlevU_ptr) -> int:
+    return load_library().nle_get_factor(h, nnz_ptr, rp_ptr, col_ptr, val_ptr, levL_ptr, levU_ptr, nlevL_ptr,
+                                         nlevU_ptr)
+
+
+def nle_destroy(h) -> None:
+    load_library().nle_destroy(h)
+
+
+# ---- convenience wrapper with torch tensors --------------------------------
+
+def _dptr(t) -> int:
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _hptr(a: np.ndarray):
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+class Eigensolver:
+    """One SPD matrix on the current CUDA device.
+
+    ``A`` is any object with ``n``, ``rowptr``, ``col``, ``val`` (numpy CSR as
+    produced by ``workloads``).  ``options`` is a dict of nle_options fields.
+    """
+
+    def __init__(self, A, options: Optional[dict] = None, stream=None):
+        import torch
+
+        self.torch = torch
+        opt = nle_default_options()
+        for k, v in (options or {}).items():
+            setattr(opt, k, v)
+        self.opt = opt
+        self.n = int(A.n)
+        self.nnz = int(A.rowptr[-1])
+        rp = np.ascontiguousarray(A.rowptr, dtype=np.int64)
+        ci = np.ascontiguousarray(A.col, dtype=np.int32)
+        va = np.ascontiguousarray(A.val, dtype=np.float64)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        st, h = nle_create(self.n, self.nnz, _hptr(rp), _hptr(ci), _hptr(va), 0, ctypes.c_void_p(self.stream.cuda_stream),
+                           opt)
+        if st != NLE_OK:
+            raise NLEError(st, nle_last_error(None))
+        self.h = h
+        self.dev = torch.device("cuda", torch.cuda.current_device())
+
+    def close(self):
+        if getattr(self, "h", None):
+            nle_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st, allow=()):
+        if st != NLE_OK and st not in allow:
+            raise NLEError(st, nle_last_error(self.h))
+        return st
+
+    def factor_ic(self, lfil: int, tau_ic: float):
+        self._check(nle_factor_ic(self.h, lfil, tau_ic))
+
+    def get_factor(self):
+        nnz = np.zeros(1, np.int64)
+        nl = np.zeros(2, np.int64)
+        self._check(nle_get_factor(self.h, _hptr(nnz), None, None, None, None, None, _hptr(nl), _hptr(nl[1:])))
+        m = int(nnz[0])
+        rp = np.zeros(self.n + 1, np.int64)
+        col = np.zeros(m, np.int32)
+        val = np.zeros(m, np.float64)
+        levL = np.zeros(self.n, np.int32)
+        levU = np.zeros(self.n, np.int32)
+        self._check(nle_get_factor(self.h, _hptr(nnz), _hptr(rp), _hptr(col), _hptr(val), _hptr(levL), _hptr(levU),
+                                   _hptr(nl), _hptr(nl[1:])))
+        return dict(Lrowptr=rp, Lcol=col, Lval=val, levL=levL, levU=levU, nlevL=int(nl[0]), nlevU=int(nl[1]))
+
+    def solve(self, p: int, tol: float, max_newton: int = 100, max_pcg: int = 20, X0=None, allow_noconv=False):
+        """Returns (lambda (p,), V (p, n), stats dict) as float64 CUDA tensors."""
+        torch = self.torch
+        lam = torch.empty(p, dtype=torch.float64, device=self.dev)
+        V = torch.empty((p, self.n), dtype=torch.float64, device=self.dev)
+        x0 = None
+        if X0 is not None:
+            x0 = torch.as_tensor(X0, dtype=torch.float64).to(self.dev).contiguous()
+        stats = nle_stats()
+        st = nle_solve(self.h, p, tol, max_newton, max_pcg, _dptr(x0) if x0 is not None else None, _dptr(lam),
+                       _dptr(V), stats, 1)
+        self._check(st, allow=(5,) if allow_noconv else ())
+        return lam, V, stats_dict(stats)
+
+    def apply_shifted(self, theta: float, x):
+        torch = self.torch
+        x = torch.as_tensor(x, dtype=torch.float64).to(self.dev).contiguous()
+        y = torch.empty_like(x)
+        self._check(nle_apply_shifted(self.h, theta, _dptr(x), _dptr(y), 1))
+        return y
+
+    def apply_prec(self, g, S=None, R=None, Q=None):
+        torch = self.torch
+        g = torch.as_tensor(g, dtype=torch.float64).to(self.dev).contiguous()
+        k = 0 if S is None else len(S)
+        m = 0 if Q is None else len(Q)
+        St = torch.as_tensor(np.asarray(S), dtype=torch.float64).to(self.dev).contiguous() if k else None
+        Rt = torch.as_tensor(np.asarray(R), dtype=torch.float64).to(self.dev).contiguous() if k else None
+        Qt = torch.as_tensor(np.asarray(Q), dtype=torch.float64).to(self.dev).contiguous() if m else None
+        c = torch.empty_like(g)
+        self._check(nle_apply_prec(self.h, k, _dptr(St) if k else None, _dptr(Rt) if k else None, m,
+                                   _dptr(Qt) if m else None, _dptr(g), _dptr(c), 1))
+        return c
+
+    def pcg(self, theta: float, tol: float, max_pcg: int, r, Q, S=None, R=None):
+        """One inner solve; Q is (m, n) with the current iterate as its last row."""
+        torch = self.torch
+        r = torch.as_tensor(r, dtype=torch.float64).to(self.dev).contiguous()
+        Qt = torch.as_tensor(np.asarray(Q), dtype=torch.float64).to(self.dev).contiguous()
+        k = 0 if S is None else len(S)
+        St = torch.as_tensor(np.asarray(S), dtype=torch.float64).to(self.dev).contiguous() if k else None
+        Rt = torch.as_tensor(np.asarray(R), dtype=torch.float64).to(self.dev).contiguous() if k else None
+        s = torch.empty_like(r)
+        info = nle_pcg_info()
+        self._check(nle_pcg(self.h, theta, tol, max_pcg, _dptr(r), Qt.shape[0], _dptr(Qt), k,
+                            _dptr(St) if k else None, _dptr(Rt) if k else None, _dptr(s), info, 1))
+        return s, dict(its=info.its, exit=EXITS[info.exit], gnorm0=info.gnorm0, gnorm=info.gnorm, eigres=info.eigres)
+
+
+def stats_dict(s: nle_stats) -> dict:
+    p = s.p
+    return dict(p=p, dacg_its=list(s.dacg_its[:p]), outer_its=list(s.outer_its[:p]), pcg_its=list(s.pcg_its[:p]),
+                converged=[bool(x) for x in s.converged[:p]], final_res=list(s.final_res[:p]),
+                mvp_dacg=int(s.mvp_dacg), mvp_newton=int(s.mvp_newton),
+                exits={EXITS[i]: int(s.exit_count[i]) for i in range(5)}, ms_dacg=float(s.ms_dacg),
+                ms_newton=float(s.ms_newton), pcg_iterations=int(s.pcg_iterations), pcg_sum_m=int(s.pcg_sum_m),
+                pcg_sum_k=int(s.pcg_sum_k), dacg_iterations=int(s.dacg_iterations), dacg_sum_m=int(s.dacg_sum_m),
+                kernel_launches=int(s.kernel_launches), ascending=bool(s.ascending))

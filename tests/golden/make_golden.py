@@ -1,0 +1,49 @@
+"""Write the stored expected values used by the full-size parity tests.
+
+Every value comes from the oracle (``oracle/``) run on the seeded workloads
+of ``workloads/``; nothing here calls the CUDA library.  Usage:
+
+    python tests/golden/make_golden.py diff3d7_100 [more workload names]
+
+Each run writes tests/golden/<name>.json with the eigenvalues, the oracle's
+iteration counts, and a seeded sample of eigenvector entries (sign
+convention: entry of largest modulus positive).
+"""
+import json
+import os
+import sys
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
+
+import oracle as O  # noqa: E402
+import workloads as W  # noqa: E402
+
+
+def main(names):
+    for name in names:
+        A, st = W.workload(name)
+        p = st["p"]
+        opt = O.OracleOptions(tol=st["tol"], lfil=st["lfil"], tau_ic=st["tau_ic"])
+        X0 = W.start_vectors(A.n, p, st["seed"])
+        t0 = time.time()
+        lam, V, stats = O.dacg_newton(A, p, X0, opt)
+        sec = time.time() - t0
+        rng = W.rng_for(st["seed"] + 99)
+        idx = np.sort(rng.choice(A.n, size=64, replace=False))
+        out = dict(workload=name, n=A.n, nnz=A.nnz, p=p, tol=st["tol"], lfil=st["lfil"], tau_ic=st["tau_ic"],
+                   lam=[float(x) for x in lam], sample_index=[int(i) for i in idx],
+                   sample_V=[[float(V[i, j]) for i in idx] for j in range(p)],
+                   oracle_seconds=sec, oracle_stats={k: stats[k] for k in
+                                                     ("dacg_its", "outer_its", "pcg_its", "converged", "final_res",
+                                                      "ascending", "nnz_L", "sigma")})
+        with open(os.path.join(HERE, f"{name}.json"), "w") as fh:
+            json.dump(out, fh, indent=1)
+        print(name, sec, lam)
+
+
+if __name__ == "__main__":
+    main(sys.argv[1:])

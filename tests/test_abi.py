@@ -1,0 +1,91 @@
+"""The C-ABI library builds, loads and exports every symbol include/nle.h
+declares; host-side argument and CSR validation work without a GPU."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1312_1553_gb300 import _build, nle
+
+    _build.build()
+    return nle.load_library()
+
+
+def declared_functions():
+    with open(os.path.join(ROOT, "include", "nle.h")) as fh:
+        txt = fh.read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(nle_[a-z_]+)\s*\(", txt)))
+
+
+def test_exports_every_declared_symbol(lib):
+    from paper_1312_1553_gb300 import nle
+
+    decl = declared_functions()
+    assert len(decl) >= 12
+    assert sorted(nle.EXPORTS) == decl
+    for name in decl:
+        assert hasattr(lib, name), name
+
+
+def test_default_options(lib):
+    from paper_1312_1553_gb300 import nle
+
+    o = nle.nle_default_options()
+    assert o.k_max == 5 and o.tau_pcg == 1e-2 and o.tau_dacg == 1e-2 and o.max_dacg == 5000
+    assert o.precision == nle.NLE_FP64 and o.exit_eigres == 1 and o.exit_stagnation == 1
+
+
+def _create(A, opt=None):
+    from paper_1312_1553_gb300 import nle
+
+    rp = np.ascontiguousarray(A.rowptr, np.int64)
+    ci = np.ascontiguousarray(A.col, np.int32)
+    va = np.ascontiguousarray(A.val, np.float64)
+    st, h = nle.nle_create(A.n, int(rp[-1]), rp.ctypes.data, ci.ctypes.data, va.ctypes.data, 0, None, opt)
+    return st, h, nle.nle_last_error(None)
+
+
+def test_argument_errors_without_device(lib):
+    A = W.tridiag(5)
+    bad = W.CSR(1, np.array([0, 1], np.int64), np.array([0], np.int32), np.array([1.0]))
+    st, h, msg = _create(bad)
+    assert st == 1 and not h.value
+    from paper_1312_1553_gb300 import nle
+
+    o = nle.nle_default_options()
+    o.k_max = 99
+    st, h, msg = _create(A, o)
+    assert st == 1 and "k_max" in msg
+
+
+@pytest.mark.parametrize("case", ["unsorted", "asym", "nodiag", "negdiag"])
+def test_csr_validation_without_device(lib, case):
+    A = W.tridiag(6)
+    rp, col, val = A.rowptr.copy(), A.col.copy(), A.val.copy()
+    if case == "unsorted":
+        col[1], col[2] = col[2], col[1]
+        expect = 2
+    elif case == "asym":
+        val[1] = -0.5
+        expect = 2
+    elif case == "nodiag":
+        # drop the diagonal of row 0 (and the symmetric partner keeps the pattern asymmetric)
+        rp = np.array([0] + list(A.rowptr[1:] - 1), np.int64)
+        col = np.delete(col, 0)
+        val = np.delete(val, 0)
+        expect = 2
+    else:
+        val[0] = -1.0
+        expect = 3
+    st, h, msg = _create(W.CSR(6, rp, col, val))
+    assert st == expect, msg
