@@ -96,6 +96,8 @@ typedef struct {
   int dacg_recompute;    /* recompute A x in DACG every this many iterations (default 50) */
   double spin_timeout_s; /* bound on each device-side wait, seconds (default 2.0) */
   int grid_ctas;         /* persistent grid size; 0 = one CTA per SM (default 0) */
+  int trsv_warps;        /* warps per CTA in the triangular solves, 1..16 (default 16) */
+  int spin_sleep_ns;     /* back-off between polls of an unfinished row, ns (default 0) */
 } nle_options;
 
 /* Per-solve statistics, mirroring the columns of the paper's tables
@@ -119,6 +121,9 @@ typedef struct {
   int64_t dacg_iterations;      /* total DACG iterations */
   int64_t dacg_sum_m;           /* sum over DACG iterations of the deflated columns */
   int64_t kernel_launches;      /* CUDA kernels this call launched */
+  double ms_phase[8];           /* device time by pass: SpMV, vector update, forward solve,
+                                   backward solve, dot products, direction, outer FP64 step,
+                                   other (Gram matrices) */
   int ascending;                /* 1 when eigenvalues came out strictly ascending */
 } nle_stats;
 

@@ -156,7 +156,7 @@ struct nle_ctx {
   int ldq = 0;
   // device memory
   DBuf d_perm, d_iperm;
-  DBuf A_sptr, A_col, A_val, A64_val, L_sptr, L_col, L_val, U_sptr, U_col, U_val, d_diag, d_sub, d_nsub;
+  DBuf A_sptr, A_col, A_val, A64_val, L_rp, L_col, L_val, U_rp, U_col, U_val, d_diag, d_pairdep;
   DBuf vecs;   // working-precision vectors
   DBuf vec64;  // Au, r, t
   DBuf dQ, dQt, dS, dR;
@@ -220,11 +220,14 @@ static Dev<T> make_dev(nle_t h) {
   const int64_t ns = h->npad / (32 * h->vw);
   D.A = {ns, h->A_sptr.as<int64_t>(), h->A_col.as<int32_t>(), h->A_val.as<T>()};
   D.A64 = {ns, h->A_sptr.as<int64_t>(), h->A_col.as<int32_t>(), h->A64_val.as<double>()};
-  D.L = {ns, h->L_sptr.as<int64_t>(), h->L_col.as<int32_t>(), h->L_val.as<T>()};
-  D.U = {ns, h->U_sptr.as<int64_t>(), h->U_col.as<int32_t>(), h->U_val.as<T>()};
+  D.Lrp = h->L_rp.as<int32_t>();
+  D.Lcol = h->L_col.as<int32_t>();
+  D.Lval = h->L_val.as<T>();
+  D.Urp = h->U_rp.as<int32_t>();
+  D.Ucol = h->U_col.as<int32_t>();
+  D.Uval = h->U_val.as<T>();
   D.diag = h->d_diag.as<T>();
-  D.sub = h->d_sub.as<uint8_t>();
-  D.nsub = h->d_nsub.as<uint8_t>();
+  D.pairdep = h->d_pairdep.as<uint8_t>();
   const int64_t np = h->npad, ext = h->npad + 32 * h->vw;
   T *v = h->vecs.as<T>();
   D.p = v + 0 * np;
@@ -264,6 +267,8 @@ static Opts make_opts(nle_t h, double tol, int max_newton, int max_pcg) {
   O.exit_stag = h->opt.exit_stagnation;
   O.recompute = h->opt.dacg_recompute;
   O.spin_ns = (long long)(h->opt.spin_timeout_s * 1e9);
+  O.trsv_warps = h->opt.trsv_warps;
+  O.spin_sleep_ns = h->opt.spin_sleep_ns;
   return O;
 }
 
@@ -350,6 +355,8 @@ void nle_default_options(nle_options *o) {
   o->dacg_recompute = 50;
   o->spin_timeout_s = 2.0;
   o->grid_ctas = 0;
+  o->trsv_warps = 16;
+  o->spin_sleep_ns = 0;
 }
 
 const char *nle_last_error(nle_t h) { return h ? h->err.c_str() : g_create_error.c_str(); }
@@ -377,6 +384,8 @@ nle_status nle_create(int64_t n, int64_t nnz, const int64_t *rowptr, const int32
   if (h->opt.k_max < 0 || h->opt.k_max > NLE_MAX_KMAX) return fail(nullptr, NLE_ERR_ARG, "k_max out of range");
   if (h->opt.precision != NLE_FP64 && h->opt.precision != NLE_MIXED) return fail(nullptr, NLE_ERR_ARG, "bad precision");
   if (!(h->opt.spin_timeout_s > 0)) return fail(nullptr, NLE_ERR_ARG, "spin_timeout_s must be positive");
+  if (h->opt.trsv_warps < 1 || h->opt.trsv_warps > NWARP) return fail(nullptr, NLE_ERR_ARG, "trsv_warps out of range");
+  if (h->opt.spin_sleep_ns < 0 || h->opt.spin_sleep_ns > 100000) return fail(nullptr, NLE_ERR_ARG, "spin_sleep_ns out of range");
   h->n = n;
   h->nnz = nnz;
   h->rowptr.resize(n + 1);
@@ -447,15 +456,14 @@ nle_status nle_factor_ic(nle_t h, int lfil, double tau_ic) {
     NLE_CUDA(h, upload(h->A_col, S.A.col));
     NLE_CUDA(h, upload(h->A_val, S.A.val));
     NLE_CUDA(h, upload(h->A64_val, S.A64.val));
-    NLE_CUDA(h, upload(h->L_sptr, S.L.sptr));
+    NLE_CUDA(h, upload(h->L_rp, S.L.rp));
     NLE_CUDA(h, upload(h->L_col, S.L.col));
     NLE_CUDA(h, upload(h->L_val, S.L.val));
-    NLE_CUDA(h, upload(h->U_sptr, S.U.sptr));
+    NLE_CUDA(h, upload(h->U_rp, S.U.rp));
     NLE_CUDA(h, upload(h->U_col, S.U.col));
     NLE_CUDA(h, upload(h->U_val, S.U.val));
     NLE_CUDA(h, upload(h->d_diag, S.diag));
-    NLE_CUDA(h, upload(h->d_sub, S.sub));
-    NLE_CUDA(h, upload(h->d_nsub, S.nsub));
+    NLE_CUDA(h, upload(h->d_pairdep, S.pairdep));
   } else {
     SellSet<double> S;
     build_sell<double>(P, H, S);
@@ -463,15 +471,14 @@ nle_status nle_factor_ic(nle_t h, int lfil, double tau_ic) {
     NLE_CUDA(h, upload(h->A_col, S.A.col));
     NLE_CUDA(h, upload(h->A_val, S.A.val));
     NLE_CUDA(h, upload(h->A64_val, S.A64.val));
-    NLE_CUDA(h, upload(h->L_sptr, S.L.sptr));
+    NLE_CUDA(h, upload(h->L_rp, S.L.rp));
     NLE_CUDA(h, upload(h->L_col, S.L.col));
     NLE_CUDA(h, upload(h->L_val, S.L.val));
-    NLE_CUDA(h, upload(h->U_sptr, S.U.sptr));
+    NLE_CUDA(h, upload(h->U_rp, S.U.rp));
     NLE_CUDA(h, upload(h->U_col, S.U.col));
     NLE_CUDA(h, upload(h->U_val, S.U.val));
     NLE_CUDA(h, upload(h->d_diag, S.diag));
-    NLE_CUDA(h, upload(h->d_sub, S.sub));
-    NLE_CUDA(h, upload(h->d_nsub, S.nsub));
+    NLE_CUDA(h, upload(h->d_pairdep, S.pairdep));
   }
   NLE_CUDA(h, upload(h->d_perm, h->perm));
   NLE_CUDA(h, upload(h->d_iperm, h->iperm));
@@ -597,6 +604,7 @@ static nle_status solve_impl(nle_t h, int p, double tol, int max_newton, int max
     stats->dacg_iterations = st.dacg_total;
     stats->dacg_sum_m = st.dacg_sum_m;
     stats->kernel_launches = launches;
+    for (int q = 0; q < 8; q++) stats->ms_phase[q] = st.tphase[q] * 1e-6;
     stats->ascending = asc ? 1 : 0;
   }
   if (!allconv) return fail(h, NLE_ERR_NOCONV, "some eigenpairs reached max_newton");

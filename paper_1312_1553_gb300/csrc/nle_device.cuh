@@ -146,13 +146,28 @@ struct Shared {
   double qv[MMAX];             // Q^T v of the current projection
   int order[KMAX];             // chronological -> physical pair slot
   int ok;                      // error word broadcast after each barrier
+  long long tlast;             // phase timer (CTA 0, thread 0)
+  long long tacc[8];
 };
 
 struct Ctl {
   unsigned epoch;  // barriers passed by this CTA (thread 0 only)
   int rbuf;        // reduction buffer parity
   long long spin_ns;
+  int twarps;      // warps of this CTA that take part in the triangular solves
+  int sleep_ns;    // poll back-off
 };
+
+// Phase timers: CTA 0 / thread 0 charges the time since the last mark to
+// `phase` (called right after a barrier, so the time covers the whole grid).
+enum { PH_SPMV = 0, PH_UPDATE = 1, PH_FWD = 2, PH_BWD = 3, PH_DOTS = 4, PH_DIR = 5, PH_OUTER = 6, PH_OTHER = 7 };
+__device__ __forceinline__ void tmark(Shared &sh, int phase) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const long long t = gtimer();
+    sh.tacc[phase] += t - sh.tlast;
+    sh.tlast = t;
+  }
+}
 
 // Grid-wide barrier for a cooperative launch.  Monotone counter: barrier
 // number e completes when the counter reaches e * gridDim.x.  Every wait is
@@ -290,9 +305,10 @@ __device__ __forceinline__ void sell_rows(const Sell<TV> &M, const TX *__restric
 
 // Wait (bounded) for a solve output to leave the not-yet-computed state.
 template <typename T>
-__device__ __noinline__ T spin_value(const T *p, T v, State *st, long long spin_ns) {
+__device__ __noinline__ T spin_value(const T *p, T v, State *st, long long spin_ns, int sleep_ns) {
   const long long t0 = gtimer();
   while (is_sent(v)) {
+    if (sleep_ns > 0) __nanosleep(sleep_ns);
     v = ld_relaxed(p);
     if (is_sent(v) && gtimer() - t0 > spin_ns) {
       record_error(st, 8 /*NLE_ERR_TIMEOUT*/, 100);
@@ -302,119 +318,75 @@ __device__ __noinline__ T spin_value(const T *p, T v, State *st, long long spin_
   return v;
 }
 
-// One chunk of a sync-free triangular solve.  LOWER: dependencies of row r
-// are positions < r; otherwise positions > r (the mirrored sweep).
-// Rows are in level order, so a slice (the 32 chunks of one warp) holds a
-// run of consecutive levels; sub[row] is the level of the row minus the
-// lowest level in its slice and nsub[slice] the number of levels in it.
-// The warp handles the levels of its slice in rounds (ascending for the
-// lower solve, descending for the upper one) separated by __syncwarp, so a
-// lane never waits for another lane of its own warp: dependencies inside
-// the slice were published in an earlier round, dependencies inside the
-// chunk come from registers, and only rows of other warps are polled.
-template <bool LOWER, typename T>
-__device__ __forceinline__ void solve_chunk(const Sell<T> &M, const T *__restrict__ diag,
-                                            const uint8_t *__restrict__ sub, const uint8_t *__restrict__ nsub,
-                                            T *xvec, int64_t chunk, const T (&rhs)[VT<T>::W],
-                                            T (&xsol)[VT<T>::W], State *st, long long spin_ns) {
-  constexpr int W = VT<T>::W;
-  constexpr int H = 32 * W;
-  const int64_t slice = chunk >> 5;
-  const int lanepos = (int)(chunk & 31);
-  const int64_t base = __ldg(M.sptr + slice);
-  const int width = (int)((__ldg(M.sptr + slice + 1) - base) / H);
-  const int64_t r0 = chunk * W;
-  const int rounds = __ldg(nsub + slice);
-  int rs[W];
-#pragma unroll
-  for (int v = 0; v < W; v++) rs[v] = __ldg(sub + r0 + v);
-  const int64_t off0 = base + (int64_t)lanepos * W;
-  T dg[W];
-  ldr(diag + r0, dg);
-  for (int rr = 0; rr < rounds; rr++) {
-    const int rnd = LOWER ? rr : rounds - 1 - rr;
-    bool act[W];
-    bool any = false;
-#pragma unroll
-    for (int v = 0; v < W; v++) {
-      act[v] = (rs[v] == rnd);
-      any = any || act[v];
+// Sync-free triangular solve over rows in level order (CSR of the strictly
+// triangular part, int32 row pointers, diagonal separate).  A warp works on
+// two consecutive rows at a time, 16 lanes per row, one matrix entry per
+// lane: every dependency of a row is fetched and, if not yet computed,
+// polled in parallel, so a row costs one L2 round trip once its inputs
+// exist.  Warps take row pairs round-robin in level order (ascending for L,
+// descending for L^T); the pair of a warp is only polled by later pairs.
+// When the second row of a pair depends on the first (pairdep[pair] = 1,
+// a level boundary), the two rows are done in two rounds separated by
+// __syncwarp, so no lane ever waits for a lane of its own warp.
+template <typename T>
+struct TriRows {
+  const int32_t *rp;       // npad + 1
+  const int32_t *col;
+  const T *val;
+  const T *diag;           // npad
+  const uint8_t *pairdep;  // npad / 2
+};
+
+template <bool LOWER, typename T, typename RHS>
+__device__ __forceinline__ void trsv_rows(const TriRows<T> &M, T *x, int64_t npad, int twarps, long long spin_ns,
+                                          int sleep_ns, State *st, RHS rhs_of) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (warp >= twarps) return;
+  const int64_t nw = (int64_t)gridDim.x * twarps;
+  const int64_t npair = npad >> 1;
+  const int q = lane >> 4, g = lane & 15;
+  for (int64_t it = (int64_t)blockIdx.x * twarps + warp; it < npair; it += nw) {
+    const int64_t pr = LOWER ? it : npair - 1 - it;
+    const int64_t r = 2 * pr + q;
+    const int e0 = __ldg(M.rp + r), e1 = __ldg(M.rp + r + 1);
+    const bool dep = __ldg(M.pairdep + pr) != 0;
+    // matrix entries of this lane (up to 3 without a loop; more in a loop)
+    int c0 = 0, c1 = 0, c2 = 0;
+    T a0 = T(0), a1 = T(0), a2 = T(0);
+    const int ea = e0 + g, eb = ea + 16, ec = eb + 16;
+    if (ea < e1) c0 = __ldg(M.col + ea), a0 = __ldg(M.val + ea);
+    if (eb < e1) c1 = __ldg(M.col + eb), a1 = __ldg(M.val + eb);
+    if (ec < e1) c2 = __ldg(M.col + ec), a2 = __ldg(M.val + ec);
+    T rhs = T(0), dg = T(1);
+    if (g == 0) {
+      rhs = rhs_of(r);
+      dg = __ldg(M.diag + r);
     }
-    if (any) {
-      T acc[W];
-      T cin[W][W];  // coupling to rows of the same chunk: cin[v][d] multiplies x[r0+d]
-#pragma unroll
-      for (int v = 0; v < W; v++) {
-        acc[v] = rhs[v];
-#pragma unroll
-        for (int d = 0; d < W; d++) cin[v][d] = T(0);
-      }
-      for (int e0 = 0; e0 < width; e0 += 2) {
-        int cc[2][W];
-        T aa[2][W];
-        T xx[2][W];
-        const bool two = (e0 + 1 < width);
-        ldr(M.col + off0 + (int64_t)e0 * H, cc[0]);
-        ldr(M.val + off0 + (int64_t)e0 * H, aa[0]);
-        if (two) {
-          ldr(M.col + off0 + (int64_t)(e0 + 1) * H, cc[1]);
-          ldr(M.val + off0 + (int64_t)(e0 + 1) * H, aa[1]);
-        } else {
-#pragma unroll
-          for (int v = 0; v < W; v++) cc[1][v] = cc[0][v], aa[1][v] = T(0);
-        }
-        // issue every external load first, then wait for the ones not ready
-#pragma unroll
-        for (int q = 0; q < 2; q++)
-#pragma unroll
-          for (int v = 0; v < W; v++) {
-            const int64_t c = cc[q][v];
-            const bool inside = (c >= r0 && c < r0 + W);
-            xx[q][v] = (inside || !act[v]) ? T(0) : ld_relaxed(xvec + c);
-          }
-#pragma unroll
-        for (int q = 0; q < 2; q++)
-#pragma unroll
-          for (int v = 0; v < W; v++) {
-            if (!act[v]) continue;
-            const int64_t c = cc[q][v];
-            const bool inside = (c >= r0 && c < r0 + W);
-            if (inside) {
-#pragma unroll
-              for (int d = 0; d < W; d++)
-                if (c - r0 == d) cin[v][d] += aa[q][v];
-            } else {
-              T xv = xx[q][v];
-              if (is_sent(xv)) xv = spin_value(xvec + c, xv, st, spin_ns);
-              acc[v] -= aa[q][v] * xv;
-            }
-          }
-      }
-      if (LOWER) {
-#pragma unroll
-        for (int v = 0; v < W; v++) {
-          if (!act[v]) continue;
-          T t = acc[v];
-#pragma unroll
-          for (int d = 0; d < W; d++)
-            if (d < v) t -= cin[v][d] * xsol[d];
-          xsol[v] = t / dg[v];
-          st_relaxed(xvec + r0 + v, xsol[v]);
-        }
-      } else {
-#pragma unroll
-        for (int v = W - 1; v >= 0; v--) {
-          if (!act[v]) continue;
-          T t = acc[v];
-#pragma unroll
-          for (int d = 0; d < W; d++)
-            if (d > v) t -= cin[v][d] * xsol[d];
-          xsol[v] = t / dg[v];
-          st_relaxed(xvec + r0 + v, xsol[v]);
+    const int rounds = dep ? 2 : 1;
+    for (int rd = 0; rd < rounds; rd++) {
+      const bool active = !dep || (LOWER ? q == rd : q == 1 - rd);
+      T acc = T(0);
+      if (active) {
+        T x0 = T(0), x1 = T(0), x2 = T(0);
+        if (ea < e1) x0 = ld_relaxed(x + c0);
+        if (eb < e1) x1 = ld_relaxed(x + c1);
+        if (ec < e1) x2 = ld_relaxed(x + c2);
+        if (is_sent(x0)) x0 = spin_value(x + c0, x0, st, spin_ns, sleep_ns);
+        if (is_sent(x1)) x1 = spin_value(x + c1, x1, st, spin_ns, sleep_ns);
+        if (is_sent(x2)) x2 = spin_value(x + c2, x2, st, spin_ns, sleep_ns);
+        acc = a0 * x0 + a1 * x1 + a2 * x2;
+        for (int e = ec + 16; e < e1; e += 16) {
+          const int c = __ldg(M.col + e);
+          T xv = ld_relaxed(x + c);
+          if (is_sent(xv)) xv = spin_value(x + c, xv, st, spin_ns, sleep_ns);
+          acc += __ldg(M.val + e) * xv;
         }
       }
+#pragma unroll
+      for (int o = 8; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (active && g == 0) st_relaxed(x + r, (rhs - acc) / dg);
+      if (dep) __syncwarp();
     }
-    if (rounds > 1) __syncwarp();
   }
 }
 

@@ -67,6 +67,8 @@ struct State {
   int err;
   int err_where;
   unsigned bar;  // grid barrier counter
+  unsigned qf, qb;  // work queues (slices) of the forward / backward solve
+  long long tphase[8];  // device time per phase (ns, measured by CTA 0)
 };
 
 struct Opts {
@@ -81,6 +83,8 @@ struct Opts {
   int exit_stag;
   int recompute;
   long long spin_ns;
+  int trsv_warps;     // warps per CTA that take part in the triangular solves
+  int spin_sleep_ns;  // back-off between polls of a not-yet-computed value
 };
 
 // Pointers handed to the persistent kernels (by value).
@@ -92,11 +96,12 @@ struct Dev {
   int ldq = 0;          // allocated columns of Q / Qt
   Sell<T> A;            // A in working precision
   Sell<double> A64;     // A in FP64 (same pattern and layout as A)
-  Sell<T> L;            // strictly lower part of L (level order)
-  Sell<T> U;            // strictly upper part of U = L^T (level order)
-  const T *diag = nullptr;  // diagonal of L
-  const uint8_t *sub = nullptr;   // level of each row minus the lowest level of its slice
-  const uint8_t *nsub = nullptr;  // number of levels in each slice
+  // strictly lower part of L and strictly upper part of U = L^T, level
+  // order, CSR with int32 row pointers (npad + 1), diagonal separate
+  const int32_t *Lrp = nullptr, *Lcol = nullptr, *Urp = nullptr, *Ucol = nullptr;
+  const T *Lval = nullptr, *Uval = nullptr;
+  const T *diag = nullptr;           // diagonal of L (1 on padding rows)
+  const uint8_t *pairdep = nullptr;  // row 2i+1 depends on row 2i
   // working-precision vectors (npad; z and c0 have npad + 32*VW entries)
   T *p, *y, *s, *g, *z, *c0, *rT, *x, *Ax, *Ap;
   T *Q;        // npad * ldq, column c at Q + c*npad (converged v_1.. and u)

@@ -29,21 +29,45 @@ namespace nle {
 // ---------------------------------------------------------------------------
 // small helpers over the chunks owned by a thread
 // ---------------------------------------------------------------------------
-// out[i][v] += sgn * sum_c coef[c] * X_c[row]   (X column c at X + c*ld)
+// out[i][v] += sgn * sum_c coef[c] * X_c[row]   (X column c at X + c*ld),
+// four columns per step for memory-level parallelism.
 template <typename T, int RPC>
 __device__ __forceinline__ void comb_add(const T *X, int64_t ld, int ncol, const double *coef, const int *slot,
                                          const Dev<T> &D, T (&out)[RPC][VT<T>::W], double sgn) {
   constexpr int W = VT<T>::W;
   const int64_t tid = gtid(), TT = gthreads();
-  for (int c = 0; c < ncol; c++) {
+  int c = 0;
+  for (; c + 4 <= ncol; c += 4) {
+    const T *col[4];
+    T cf[4];
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+      col[u] = X + (int64_t)(slot ? slot[c + u] : c + u) * ld;
+      cf[u] = T(sgn * coef[c + u]);
+    }
+#pragma unroll
+    for (int i = 0; i < RPC; i++) {
+      const int64_t ch = tid + i * TT;
+      if (ch < D.nchunks) {
+        T q[4][W];
+#pragma unroll
+        for (int u = 0; u < 4; u++) ldc(col[u] + ch * W, q[u]);
+#pragma unroll
+        for (int u = 0; u < 4; u++)
+#pragma unroll
+          for (int v = 0; v < W; v++) out[i][v] += cf[u] * q[u][v];
+      }
+    }
+  }
+  for (; c < ncol; c++) {
     const T cf = T(sgn * coef[c]);
-    const T *col = X + (int64_t)(slot ? slot[c] : c) * ld;
+    const T *cl = X + (int64_t)(slot ? slot[c] : c) * ld;
 #pragma unroll
     for (int i = 0; i < RPC; i++) {
       const int64_t ch = tid + i * TT;
       if (ch < D.nchunks) {
         T q[W];
-        ldc(col + ch * W, q);
+        ldc(cl + ch * W, q);
 #pragma unroll
         for (int v = 0; v < W; v++) out[i][v] += cf * q[v];
       }
@@ -51,14 +75,38 @@ __device__ __forceinline__ void comb_add(const T *X, int64_t ld, int ncol, const
   }
 }
 
-// slot base.. : sum over owned rows of X_c[row] * val[i][v], for each column
+// slot0 + c: sum over owned rows of X_c[row] * val[i][v], for each column c.
+// Four columns per step so that 4*RPC independent loads are in flight.
 template <typename T, int RPC>
 __device__ __forceinline__ void dots_put(Shared &sh, int slot0, const T *X, int64_t ld, int ncol, const int *slot,
                                          const Dev<T> &D, const T (&val)[RPC][VT<T>::W], bool reverse) {
   constexpr int W = VT<T>::W;
   const int64_t tid = gtid(), TT = gthreads();
-  for (int c = 0; c < ncol; c++) {
-    const T *col = X + (int64_t)(slot ? slot[c] : c) * ld;
+  int c = 0;
+  for (; c + 4 <= ncol; c += 4) {
+    const T *col[4];
+#pragma unroll
+    for (int u = 0; u < 4; u++) col[u] = X + (int64_t)(slot ? slot[c + u] : c + u) * ld;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+    for (int i = 0; i < RPC; i++) {
+      const int64_t k = tid + i * TT;
+      const int64_t ch = reverse ? D.nchunks - 1 - k : k;
+      if (k < D.nchunks) {
+        T q[4][W];
+#pragma unroll
+        for (int u = 0; u < 4; u++) ldc(col[u] + ch * W, q[u]);
+#pragma unroll
+        for (int u = 0; u < 4; u++)
+#pragma unroll
+          for (int v = 0; v < W; v++) acc[u] += double(q[u][v]) * double(val[i][v]);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; u++) red_put(sh, slot0 + c + u, acc[u]);
+  }
+  for (; c < ncol; c++) {
+    const T *cl = X + (int64_t)(slot ? slot[c] : c) * ld;
     double acc = 0.0;
 #pragma unroll
     for (int i = 0; i < RPC; i++) {
@@ -66,7 +114,7 @@ __device__ __forceinline__ void dots_put(Shared &sh, int slot0, const T *X, int6
       const int64_t ch = reverse ? D.nchunks - 1 - k : k;
       if (k < D.nchunks) {
         T q[W];
-        ldc(col + ch * W, q);
+        ldc(cl + ch * W, q);
 #pragma unroll
         for (int v = 0; v < W; v++) acc += double(q[v]) * double(val[i][v]);
       }
@@ -160,68 +208,73 @@ __device__ bool gram(const Dev<T> &D, Shared &sh, Ctl &ctl, int m, int k) {
 // preconditioner tail: forward solve on w = g - R a, backward solve, the dot
 // products of Algorithm 3.1's forward loop and Gram-Schmidt, and the output
 // pass out = c0 - S(a+b) - Q z (+ beta * out, beta = gamma'/gamma_old when
-// use_beta).  On entry gv holds g for the owned chunks and z/c0 hold the
-// not-yet-computed marker.  *gamma_new receives gamma' = g^T c.
+// use_beta).  On entry z/c0 hold the not-yet-computed marker and the solve
+// queues are reset.  *gamma_new receives gamma' = g^T c.
+//
+// The triangular solves run on ctl.twarps warps per CTA (trsv_rows): every
+// row pair is taken after all lower pairs (higher, for L^T) by resident
+// warps, so every wait ends (co-residency comes from the cooperative launch).
 // ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void trsv_forward(const Dev<T> &D, Shared &sh, const Ctl &ctl, int k) {
+  const TriRows<T> L{D.Lrp, D.Lcol, D.Lval, D.diag, D.pairdep};
+  trsv_rows<true, T>(L, D.z, D.npad, ctl.twarps, ctl.spin_ns, ctl.sleep_ns, D.st, [&](int64_t r) {
+    T w = __ldcg(D.g + r);
+    for (int t = 0; t < k; t++) w -= T(sh.a[t]) * __ldcg(D.R + (int64_t)sh.order[t] * D.npad + r);
+    return w;
+  });
+}
+
+template <typename T>
+__device__ __forceinline__ void trsv_backward(const Dev<T> &D, const Ctl &ctl) {
+  const TriRows<T> U{D.Urp, D.Ucol, D.Uval, D.diag, D.pairdep};
+  trsv_rows<false, T>(U, D.c0, D.npad, ctl.twarps, ctl.spin_ns, ctl.sleep_ns, D.st,
+                      [&](int64_t r) { return __ldcg(D.z + r); });
+}
+
+template <typename T>
+__device__ __forceinline__ void reset_queues(const Dev<T> &D) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    D.st->qf = 0u;
+    D.st->qb = 0u;
+  }
+}
+
 template <typename T, int RPC>
-__device__ bool precond_tail(const Dev<T> &D, Shared &sh, Ctl &ctl, int m, int k, const T (&gv)[RPC][VT<T>::W],
-                             T *out, double gamma_old, bool use_beta, double *gamma_new) {
+__device__ bool precond_tail(const Dev<T> &D, Shared &sh, Ctl &ctl, int m, int k, T *out, double gamma_old,
+                             bool use_beta, double *gamma_new) {
   constexpr int W = VT<T>::W;
   const int64_t tid = gtid(), TT = gthreads();
-  // forward solve L z = w, w = g - R a
+  trsv_forward<T>(D, sh, ctl, k);
+  if (!grid_sync(D.st, sh, ctl, 20)) return false;
+  tmark(sh, PH_FWD);
+  trsv_backward<T>(D, ctl);
+  if (!grid_sync(D.st, sh, ctl, 21)) return false;
+  tmark(sh, PH_BWD);
+  // dot products of c0: slots [0,k) r_t^T c0 ; k: g^T c0 ; [k+1, k+1+m) q_c^T c0
+  T cv[RPC][W];
   {
-    T w[RPC][W];
-#pragma unroll
-    for (int i = 0; i < RPC; i++)
-#pragma unroll
-      for (int v = 0; v < W; v++) w[i][v] = gv[i][v];
-    if (k > 0) comb_add<T, RPC>(D.R, D.npad, k, sh.a, sh.order, D, w, -1.0);
+    double acc = 0.0;
 #pragma unroll
     for (int i = 0; i < RPC; i++) {
       const int64_t ch = tid + i * TT;
       if (ch < D.nchunks) {
-        T zs[W];
-        solve_chunk<true, T>(D.L, D.diag, D.sub, D.nsub, D.z, ch, w[i], zs, D.st, ctl.spin_ns);
-      }
-    }
-  }
-  if (!grid_sync(D.st, sh, ctl, 20)) return false;
-  // backward solve L^T c0 = z (mirrored ownership), then the dot products
-  T cv[RPC][W];
-  {
+        T gg[W];
+        ldc(D.c0 + ch * W, cv[i]);
+        ldc(D.g + ch * W, gg);
 #pragma unroll
-    for (int i = 0; i < RPC; i++) {
-      const int64_t kk = tid + i * TT;
-      if (kk < D.nchunks) {
-        const int64_t ch = D.nchunks - 1 - kk;
-        T zz[W];
-        ldc(D.z + ch * W, zz);
-        solve_chunk<false, T>(D.U, D.diag, D.sub, D.nsub, D.c0, ch, zz, cv[i], D.st, ctl.spin_ns);
+        for (int v = 0; v < W; v++) acc += double(gg[v]) * double(cv[i][v]);
       } else {
 #pragma unroll
         for (int v = 0; v < W; v++) cv[i][v] = T(0);
       }
     }
-    // slots: [0,k) r_t^T c0 ; k: g^T c0 ; [k+1, k+1+m) q_c^T c0
-    dots_put<T, RPC>(sh, 0, D.R, D.npad, k, sh.order, D, cv, true);
-    {
-      double acc = 0.0;
-#pragma unroll
-      for (int i = 0; i < RPC; i++) {
-        const int64_t kk = tid + i * TT;
-        if (kk < D.nchunks) {
-          const int64_t ch = D.nchunks - 1 - kk;
-          T gg[W];
-          ldc(D.g + ch * W, gg);
-#pragma unroll
-          for (int v = 0; v < W; v++) acc += double(gg[v]) * double(cv[i][v]);
-        }
-      }
-      red_put(sh, k, acc);
-    }
-    dots_put<T, RPC>(sh, k + 1, D.Q, D.npad, m, nullptr, D, cv, true);
+    red_put(sh, k, acc);
+    dots_put<T, RPC>(sh, 0, D.R, D.npad, k, sh.order, D, cv, false);
+    dots_put<T, RPC>(sh, k + 1, D.Q, D.npad, m, nullptr, D, cv, false);
   }
-  if (!reduce_all(D, sh, ctl, k + 1 + m, 21)) return false;
+  if (!reduce_all(D, sh, ctl, k + 1 + m, 22)) return false;
+  tmark(sh, PH_DOTS);
   const double gc0 = sh.sc[k];
   coef_b(sh, k, m, sh.sc, sh.sc + k + 1);
   // gamma' = g^T c = g^T c0 - (S^T g)(a+b)   (g is orthogonal to Q)
@@ -229,21 +282,10 @@ __device__ bool precond_tail(const Dev<T> &D, Shared &sh, Ctl &ctl, int m, int k
   for (int s = 0; s < k; s++) gnew -= sh.sg[s] * sh.ab[s];
   *gamma_new = gnew;
   const double beta = use_beta ? gnew / gamma_old : 0.0;
-  // output pass (natural ownership): out = c0 - S ab - Q z + beta*out
+  // output pass: out = c0 - S ab - Q z + beta*out
   {
-    T o[RPC][W];
-#pragma unroll
-    for (int i = 0; i < RPC; i++) {
-      const int64_t ch = tid + i * TT;
-      if (ch < D.nchunks) {
-        ldc(D.c0 + ch * W, o[i]);
-      } else {
-#pragma unroll
-        for (int v = 0; v < W; v++) o[i][v] = T(0);
-      }
-    }
-    if (k > 0) comb_add<T, RPC>(D.S, D.npad, k, sh.ab, sh.order, D, o, -1.0);
-    if (m > 0) comb_add<T, RPC>(D.Q, D.npad, m, sh.zq, nullptr, D, o, -1.0);
+    if (k > 0) comb_add<T, RPC>(D.S, D.npad, k, sh.ab, sh.order, D, cv, -1.0);
+    if (m > 0) comb_add<T, RPC>(D.Q, D.npad, m, sh.zq, nullptr, D, cv, -1.0);
 #pragma unroll
     for (int i = 0; i < RPC; i++) {
       const int64_t ch = tid + i * TT;
@@ -252,13 +294,15 @@ __device__ bool precond_tail(const Dev<T> &D, Shared &sh, Ctl &ctl, int m, int k
           T po[W];
           ldc(out + ch * W, po);
 #pragma unroll
-          for (int v = 0; v < W; v++) o[i][v] += T(beta) * po[v];
+          for (int v = 0; v < W; v++) cv[i][v] += T(beta) * po[v];
         }
-        stv(out + ch * W, o[i]);
+        stv(out + ch * W, cv[i]);
       }
     }
   }
-  return grid_sync(D.st, sh, ctl, 22);
+  const bool ok = grid_sync(D.st, sh, ctl, 23);
+  tmark(sh, PH_DIR);
+  return ok;
 }
 
 // ---------------------------------------------------------------------------
@@ -316,9 +360,11 @@ __device__ bool pcg_solve(const Dev<T> &D, const Opts &O, Shared &sh, Ctl &ctl, 
         stv(D.c0 + ch * W, sent);
       }
     }
+    reset_queues(D);
     red_put(sh, 0, self_dot<T, RPC>(gv, gv));
     dots_put<T, RPC>(sh, 1, D.S, D.npad, k, sh.order, D, gv, false);
     if (!reduce_all(D, sh, ctl, 1 + k, 31)) return false;
+    tmark(sh, PH_UPDATE);
   }
   const double g0 = sqrt(sh.sc[0]);
   if (threadIdx.x == 0)
@@ -326,7 +372,7 @@ __device__ bool pcg_solve(const Dev<T> &D, const Opts &O, Shared &sh, Ctl &ctl, 
   __syncthreads();
   coef_a(sh, k);
   double gamma;
-  if (!precond_tail<T, RPC>(D, sh, ctl, m, k, gv, D.p, 0.0, false, &gamma)) return false;
+  if (!precond_tail<T, RPC>(D, sh, ctl, m, k, D.p, 0.0, false, &gamma)) return false;
 
   res.g0 = g0;
   res.gn = g0;
@@ -361,6 +407,7 @@ __device__ bool pcg_solve(const Dev<T> &D, const Opts &O, Shared &sh, Ctl &ctl, 
       red_put(sh, 0, pty);
       dots_put<T, RPC>(sh, 1, D.Q, D.npad, m, nullptr, D, yv, false);
       if (!reduce_all(D, sh, ctl, 1 + m, 32)) return false;
+      tmark(sh, PH_SPMV);
     }
     const double delta = sh.sc[0];
     if (!(delta > 0.0)) {
@@ -405,12 +452,14 @@ __device__ bool pcg_solve(const Dev<T> &D, const Opts &O, Shared &sh, Ctl &ctl, 
           for (int v = 0; v < W; v++) gv[i][v] = T(0);
         }
       }
+      reset_queues(D);
       red_put(sh, 0, self_dot<T, RPC>(gv, gv));
       red_put(sh, 1, rs);
       red_put(sh, 2, sg);
       red_put(sh, 3, ss);
       dots_put<T, RPC>(sh, 4, D.S, D.npad, k, sh.order, D, gv, false);
       if (!reduce_all(D, sh, ctl, 4 + k, 33)) return false;
+      tmark(sh, PH_UPDATE);
     }
     const double gn = sqrt(sh.sc[0]);
     const double rs = sh.sc[1], sg = sh.sc[2], ss = sh.sc[3];
@@ -444,7 +493,7 @@ __device__ bool pcg_solve(const Dev<T> &D, const Opts &O, Shared &sh, Ctl &ctl, 
     __syncthreads();
     coef_a(sh, k);
     double gnew;
-    if (!precond_tail<T, RPC>(D, sh, ctl, m, k, gv, D.p, gamma, true, &gnew)) return false;
+    if (!precond_tail<T, RPC>(D, sh, ctl, m, k, D.p, gamma, true, &gnew)) return false;
     gamma = gnew;
     gprev = gn;
     eprev = eres;
@@ -514,15 +563,25 @@ __device__ bool fp64_residual(const Dev<T> &D, Shared &sh, Ctl &ctl, const doubl
 }
 
 template <typename T>
-__device__ void load_state(const Dev<T> &D, Shared &sh, Ctl &ctl, long long spin_ns) {
+__device__ void load_state(const Dev<T> &D, Shared &sh, Ctl &ctl, const Opts &O) {
   ctl.epoch = 0;
   ctl.rbuf = 0;
-  ctl.spin_ns = spin_ns;
+  ctl.spin_ns = O.spin_ns;
+  ctl.twarps = max(1, min(NWARP, O.trsv_warps));
+  ctl.sleep_ns = O.spin_sleep_ns;
   if (threadIdx.x == 0) {
     sh.ok = 1;
-    for (int s = 0; s < KMAX; s++) sh.order[s] = D.st->order[s];
+    for (int s = 0; s < KMAX; s++) sh.order[s] = s;
+    for (int q = 0; q < 8; q++) sh.tacc[q] = 0;
+    sh.tlast = gtimer();
   }
   __syncthreads();
+}
+
+// add this launch's phase times to the state (CTA 0)
+__device__ __forceinline__ void flush_timers(State *st, Shared &sh) {
+  if (blockIdx.x == 0 && threadIdx.x == 0)
+    for (int q = 0; q < 8; q++) st->tphase[q] += sh.tacc[q];
 }
 
 // ---------------------------------------------------------------------------
@@ -533,7 +592,7 @@ __global__ void __launch_bounds__(TPB, 1) k_newton(Dev<T> D, Opts O) {
   constexpr int W = VT<T>::W;
   __shared__ Shared sh;
   Ctl ctl;
-  load_state(D, sh, ctl, O.spin_ns);
+  load_state(D, sh, ctl, O);
   const int64_t tid = gtid(), TT = gthreads();
   const int j = D.st->j;
   const int m = j + 1;
@@ -551,9 +610,11 @@ __global__ void __launch_bounds__(TPB, 1) k_newton(Dev<T> D, Opts O) {
   double theta = sh.sc[0] / sh.sc[1];
   if (!fp64_residual<T, RPC>(D, sh, ctl, u, theta, j)) return;
   double rnorm = sqrt(sh.sc[0]);
+  tmark(sh, PH_OUTER);
   int it = 0;
   while (rnorm > O.tol * theta && it < O.max_newton) {
     if (!gram<T, RPC>(D, sh, ctl, m, k)) return;
+    tmark(sh, PH_OTHER);
     PcgOut po;
     if (!pcg_solve<T, RPC>(D, O, sh, ctl, m, k, theta, O.max_pcg, po)) return;
     mvp += po.its;
@@ -662,8 +723,10 @@ __global__ void __launch_bounds__(TPB, 1) k_newton(Dev<T> D, Opts O) {
     theta = sh.sc[0] / sh.sc[1];
     if (!fp64_residual<T, RPC>(D, sh, ctl, u, theta, j)) return;
     rnorm = sqrt(sh.sc[0]);
+    tmark(sh, PH_OUTER);
     it++;
   }
+  flush_timers(D.st, sh);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     State *st = D.st;
     st->theta = theta;
@@ -691,7 +754,7 @@ __global__ void __launch_bounds__(TPB, 1) k_dacg(Dev<T> D, Opts O) {
   constexpr int W = VT<T>::W;
   __shared__ Shared sh;
   Ctl ctl;
-  load_state(D, sh, ctl, O.spin_ns);
+  load_state(D, sh, ctl, O);
   const int64_t tid = gtid(), TT = gthreads();
   const int j = D.st->j;
   const int mq = j;  // converged eigenvectors (shadow columns of Q)
@@ -788,8 +851,10 @@ __global__ void __launch_bounds__(TPB, 1) k_dacg(Dev<T> D, Opts O) {
           stv(D.c0 + ch * W, sent);
         }
       }
+      reset_queues(D);
       red_put(sh, 0, self_dot<T, RPC>(gv, gv));
       if (!reduce_all(D, sh, ctl, 1, 55)) return;
+      tmark(sh, PH_UPDATE);
     }
     if (sqrt(sh.sc[0]) <= O.tau_dacg * q) break;
     // P3-P5: gt = (I - Q~Q~^T) Phat_0 g,  p = -gt + beta p
@@ -797,7 +862,7 @@ __global__ void __launch_bounds__(TPB, 1) k_dacg(Dev<T> D, Opts O) {
     {
       // Phat_0 g via the preconditioner tail with no pairs, writing into Ap as
       // scratch: Ap = c0 - Q z, then p = -Ap + beta p below.
-      if (!precond_tail<T, RPC>(D, sh, ctl, mq, 0, gv, D.Ap, 0.0, false, &gg)) return;
+      if (!precond_tail<T, RPC>(D, sh, ctl, mq, 0, D.Ap, 0.0, false, &gg)) return;
       const double beta = (it == 0) ? 0.0 : gg / gg_prev;
 #pragma unroll
       for (int i = 0; i < RPC; i++) {
@@ -817,6 +882,7 @@ __global__ void __launch_bounds__(TPB, 1) k_dacg(Dev<T> D, Opts O) {
         }
       }
       if (!grid_sync(D.st, sh, ctl, 56)) return;
+      tmark(sh, PH_DIR);
     }
     // P6: Ap = A p; line-search scalars
     {
@@ -844,6 +910,7 @@ __global__ void __launch_bounds__(TPB, 1) k_dacg(Dev<T> D, Opts O) {
       red_put(sh, 2, d);
       red_put(sh, 3, e);
       if (!reduce_all(D, sh, ctl, 4, 57)) return;
+      tmark(sh, PH_SPMV);
     }
     double al;
     {
@@ -887,6 +954,7 @@ __global__ void __launch_bounds__(TPB, 1) k_dacg(Dev<T> D, Opts O) {
       red_put(sh, 0, xx);
       if (!reduce_all(D, sh, ctl, 1, 58)) return;
       nx = sqrt(sh.sc[0]);
+      tmark(sh, PH_UPDATE);
     }
     its = it + 1;
     if (O.recompute > 0 && its % O.recompute == 0) {
@@ -920,6 +988,7 @@ __global__ void __launch_bounds__(TPB, 1) k_dacg(Dev<T> D, Opts O) {
       }
     }
   }
+  flush_timers(D.st, sh);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     D.st->dacg_its[j] = its;
     D.st->mvp_dacg += mvp;
@@ -958,7 +1027,7 @@ __global__ void __launch_bounds__(TPB, 1) k_prec(Dev<T> D, Opts O, int m, int k)
   constexpr int W = VT<T>::W;
   __shared__ Shared sh;
   Ctl ctl;
-  load_state(D, sh, ctl, O.spin_ns);
+  load_state(D, sh, ctl, O);
   if (threadIdx.x == 0)
     for (int s = 0; s < KMAX; s++) sh.order[s] = s;
   __syncthreads();
@@ -981,6 +1050,7 @@ __global__ void __launch_bounds__(TPB, 1) k_prec(Dev<T> D, Opts O, int m, int k)
       for (int v = 0; v < W; v++) gv[i][v] = T(0);
     }
   }
+  reset_queues(D);
   dots_put<T, RPC>(sh, 0, D.S, D.npad, k, sh.order, D, gv, false);
   if (!reduce_all(D, sh, ctl, k, 60)) return;
   if (threadIdx.x == 0)
@@ -988,7 +1058,7 @@ __global__ void __launch_bounds__(TPB, 1) k_prec(Dev<T> D, Opts O, int m, int k)
   __syncthreads();
   coef_a(sh, k);
   double gamma;
-  precond_tail<T, RPC>(D, sh, ctl, m, k, gv, D.y, 0.0, false, &gamma);
+  precond_tail<T, RPC>(D, sh, ctl, m, k, D.y, 0.0, false, &gamma);
 }
 
 // One inner solve: theta given, r in rT, Q with m columns, k pairs in slots 0..k-1.
@@ -996,7 +1066,7 @@ template <typename T, int RPC>
 __global__ void __launch_bounds__(TPB, 1) k_pcg(Dev<T> D, Opts O, int m, int k, double theta, int max_pcg) {
   __shared__ Shared sh;
   Ctl ctl;
-  load_state(D, sh, ctl, O.spin_ns);
+  load_state(D, sh, ctl, O);
   if (threadIdx.x == 0)
     for (int s = 0; s < KMAX; s++) sh.order[s] = s;
   __syncthreads();

@@ -275,29 +275,28 @@ static void pack(int64_t n, int64_t npad, int H, const std::vector<int64_t> &rp,
 }
 
 template <typename TV>
+static void tri(int64_t n, int64_t npad, const std::vector<int64_t> &rp, const std::vector<int32_t> &col,
+                const std::vector<double> &val, TriHost<TV> &out) {
+  out.rp.assign(npad + 1, 0);
+  for (int64_t i = 0; i <= npad; i++) out.rp[i] = (int32_t)rp[std::min(i, n)];
+  out.col.assign(col.begin(), col.end());
+  out.val.resize(val.size());
+  for (size_t e = 0; e < val.size(); e++) out.val[e] = TV(val[e]);
+}
+
+template <typename TV>
 void build_sell(const Permuted &P, int H, SellSet<TV> &S) {
   pack<TV>(P.n, P.npad, H, P.Arp, P.Acol, P.Aval, 0, 0, S.A);
   pack<double>(P.n, P.npad, H, P.Arp, P.Acol, P.Aval, 0, 0, S.A64);
-  pack<TV>(P.n, P.npad, H, P.Lrp, P.Lcol, P.Lval, 1, P.npad, S.L);
-  pack<TV>(P.n, P.npad, H, P.Urp, P.Ucol, P.Uval, 1, P.npad, S.U);
+  tri<TV>(P.n, P.npad, P.Lrp, P.Lcol, P.Lval, S.L);
+  tri<TV>(P.n, P.npad, P.Urp, P.Ucol, P.Uval, S.U);
   S.diag.assign(P.npad, TV(1));
   for (int64_t i = 0; i < P.n; i++) S.diag[i] = TV(P.diag[i]);
-  // rounds of the triangular solves: levels are contiguous in the relabelled
-  // order, so a slice of H rows spans levels lev[first] .. lev[last] (<= H)
-  const int64_t ns = P.npad / H;
-  S.sub.assign(P.npad, 0);
-  S.nsub.assign(ns, 1);
-  for (int64_t s = 0; s < ns; s++) {
-    const int64_t r0 = s * H;
-    if (r0 >= P.n) continue;
-    const int32_t l0 = P.lev[r0];
-    int32_t top = 0;
-    for (int64_t r = r0; r < std::min(P.n, r0 + H); r++) {
-      S.sub[r] = (uint8_t)(P.lev[r] - l0);
-      top = std::max(top, P.lev[r] - l0);
-    }
-    S.nsub[s] = (uint8_t)(top + 1);
-  }
+  // a pair of rows (2i, 2i+1) is coupled when L'(2i+1, 2i) != 0
+  S.pairdep.assign(P.npad / 2, 0);
+  for (int64_t i = 1; i < P.n; i += 2)
+    for (int64_t e = P.Lrp[i]; e < P.Lrp[i + 1]; e++)
+      if (P.Lcol[e] == i - 1) S.pairdep[i / 2] = 1;
 }
 
 template void build_sell<float>(const Permuted &, int, SellSet<float> &);

@@ -38,12 +38,19 @@ struct SellHost {
 };
 
 template <typename TV>
+struct TriHost {
+  std::vector<int32_t> rp;  // npad + 1
+  std::vector<int32_t> col;
+  std::vector<TV> val;
+};
+
+template <typename TV>
 struct SellSet {
-  SellHost<TV> A, L, U;
+  SellHost<TV> A;
   SellHost<double> A64;
-  std::vector<TV> diag;
-  std::vector<uint8_t> sub;   // per row: level minus the lowest level of its slice
-  std::vector<uint8_t> nsub;  // per slice: number of levels it spans
+  TriHost<TV> L, U;            // strictly lower / upper parts, level order
+  std::vector<TV> diag;        // npad, 1 on padding rows
+  std::vector<uint8_t> pairdep;  // npad / 2: row 2i+1 depends on row 2i
 };
 
 // 0 on success; 2 = malformed CSR, 3 = non-positive diagonal (msg says why).

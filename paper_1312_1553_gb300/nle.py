@@ -23,6 +23,7 @@ STATUS = {0: "NLE_OK", 1: "NLE_ERR_ARG", 2: "NLE_ERR_CSR", 3: "NLE_ERR_NOT_SPD",
           10: "NLE_ERR_NO_DEVICE"}
 NLE_FP64, NLE_MIXED = 0, 1
 EXITS = ("tol", "maxit", "eigres", "stagnation", "breakdown")
+PHASES = ("spmv", "update", "fwd_solve", "bwd_solve", "dots", "direction", "outer_fp64", "other")
 NLE_MAX_P = 64
 
 # every symbol include/nle.h declares
@@ -34,7 +35,8 @@ class nle_options(ctypes.Structure):
     _fields_ = [("k_max", ctypes.c_int), ("tau_pcg", ctypes.c_double), ("tau_dacg", ctypes.c_double),
                 ("max_dacg", ctypes.c_int), ("precision", ctypes.c_int), ("exit_eigres", ctypes.c_int),
                 ("exit_stagnation", ctypes.c_int), ("dacg_recompute", ctypes.c_int),
-                ("spin_timeout_s", ctypes.c_double), ("grid_ctas", ctypes.c_int)]
+                ("spin_timeout_s", ctypes.c_double), ("grid_ctas", ctypes.c_int), ("trsv_warps", ctypes.c_int),
+                ("spin_sleep_ns", ctypes.c_int)]
 
 
 class nle_stats(ctypes.Structure):
@@ -45,7 +47,7 @@ class nle_stats(ctypes.Structure):
                 ("ms_newton", ctypes.c_double), ("ms_pcg_inner", ctypes.c_double),
                 ("pcg_iterations", ctypes.c_int64), ("pcg_sum_m", ctypes.c_int64), ("pcg_sum_k", ctypes.c_int64),
                 ("dacg_iterations", ctypes.c_int64), ("dacg_sum_m", ctypes.c_int64),
-                ("kernel_launches", ctypes.c_int64), ("ascending", ctypes.c_int)]
+                ("kernel_launches", ctypes.c_int64), ("ms_phase", ctypes.c_double * 8), ("ascending", ctypes.c_int)]
 
 
 class nle_pcg_info(ctypes.Structure):
@@ -286,4 +288,5 @@ def stats_dict(s: nle_stats) -> dict:
                 exits={EXITS[i]: int(s.exit_count[i]) for i in range(5)}, ms_dacg=float(s.ms_dacg),
                 ms_newton=float(s.ms_newton), pcg_iterations=int(s.pcg_iterations), pcg_sum_m=int(s.pcg_sum_m),
                 pcg_sum_k=int(s.pcg_sum_k), dacg_iterations=int(s.dacg_iterations), dacg_sum_m=int(s.dacg_sum_m),
-                kernel_launches=int(s.kernel_launches), ascending=bool(s.ascending))
+                kernel_launches=int(s.kernel_launches),
+                ms_phase=dict(zip(PHASES, [float(x) for x in s.ms_phase])), ascending=bool(s.ascending))

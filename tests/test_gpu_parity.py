@@ -55,8 +55,11 @@ def align(v, ref):
 
 
 def sin_angle(a, b):
-    c = abs(float(a @ b)) / (np.linalg.norm(a) * np.linalg.norm(b))
-    return math.sqrt(max(0.0, 1.0 - c * c))
+    """sin of the angle between a and b as the norm of the rejection of a
+    from b (no cancellation, unlike sqrt(1 - cos^2))."""
+    a = a / np.linalg.norm(a)
+    b = b / np.linalg.norm(b)
+    return float(np.linalg.norm(a - (a @ b) * b))
 
 
 # ---------------------------------------------------------------------------
