@@ -10,8 +10,9 @@ separately (``ic_seconds``), as the paper reports its "IC CPU" column.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp64]
   python bench.py --impl reference ...    # the oracle on the host cores
 
-Under torchrun (N > 1) every rank solves its own replica of the problem
-(one problem does not shard) and rank 0 prints the line.
+Under torchrun (N > 1) every rank solves its own replica of the problem (a
+single problem does not shard: the IC triangular solves are one global
+recurrence) and rank 0 prints the line.
 """
 from __future__ import annotations
 
@@ -126,11 +127,13 @@ class ClockSampler:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        import tempfile
+
+        fd, self.path = tempfile.mkstemp(prefix=f"nle_clocks_rank{index}_", suffix=".csv")
+        os.close(fd)
 
     def start(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
                                           "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
