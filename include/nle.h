@@ -234,6 +234,43 @@ nle_status nle_pcg(nle_t h, double theta, double tol, int max_pcg, const double 
 nle_status nle_get_factor(nle_t h, int64_t *nnzL, int64_t *Lrowptr, int32_t *Lcol, double *Lval, int32_t *levL,
                           int32_t *levU, int64_t *nlevL, int64_t *nlevU);
 
+/* ---- Allocation-free preconditioner application --------------------------
+ * The paper has no counterpart to this call; it exists for callers that
+ * cannot allocate device memory when they need the preconditioner: code
+ * running inside another framework's memory pool, real-time loops in which
+ * cudaMalloc's implicit device synchronisation and latency are not
+ * acceptable, or programs that must finish all allocation at start-up.
+ *
+ * c = (L L^T)^{-1} g, the incomplete-Cholesky part P0hat of the
+ * preconditioner (Section 2), in FP64, with L given by the caller:
+ *   Lrp[n+1], Lcol, Lval: the strictly lower part of L in CSR (int32 row
+ *     pointers), rows in natural order;
+ *   Urp[n+1], Ucol, Uval: the strictly upper part of U = L^T in CSR;
+ *   diag[n]: the diagonal of L;  g[n]: input;  c[n]: output.
+ * Every pointer is a device pointer owned by the caller; stream is the
+ * cudaStream_t the work is ordered on (NULL = legacy default stream); the
+ * call returns after that work has completed.
+ *
+ * It allocates nothing: its only temporary storage is one fixed array of
+ * NLE_NOALLOC_MAX_N + 32 doubles (about 2 MB) compiled into the library,
+ * which every GPU that loads the library holds until the process exits.
+ * Consequences for the caller:
+ *   - n must be 1..NLE_NOALLOC_MAX_N; larger n returns NLE_ERR_ARG with a
+ *     message in nle_last_error(NULL) and touches no memory;
+ *   - the first call on a device looks up the array's device address once
+ *     for that device (cudaGetSymbolAddress, with that device current), so
+ *     make that first call before any stream capture;
+ *   - all calls share the array and it keeps the last call's contents (the
+ *     call resets what must start fresh), so calls that overlap on the GPU,
+ *     on any streams or threads, race: serialise them;
+ *   - entries that are not strictly triangular are skipped and reported
+ *     (NLE_ERR_CSR); a wait that runs out reports NLE_ERR_TIMEOUT.
+ */
+#define NLE_NOALLOC_MAX_N 262144
+nle_status nle_ic_apply_noalloc(int64_t n, const int32_t *Lrp, const int32_t *Lcol, const double *Lval,
+                                const int32_t *Urp, const int32_t *Ucol, const double *Uval, const double *diag,
+                                const double *g, double *c, void *stream);
+
 /* Message of the last failed call on h (or of the last nle_create failure
  * when h is NULL).  Valid until the next call on h. */
 const char *nle_last_error(nle_t h);

@@ -64,7 +64,7 @@ def build(force: bool = False, jobs: int | None = None, verbose: bool = False) -
         o = os.path.join(BUILD, f"nle_kernels_{tag}.o")
         cmds.append([nvcc, *NVFLAGS, f"-DNLE_T={typ}", f"-DNLE_RPC={rpc}", f"-DNLE_TAG={tag}", "-c", kern, "-o", o])
         objs.append(o)
-    for src in ("nle_api.cu", "nle_setup.cpp"):
+    for src in ("nle_api.cu", "nle_setup.cpp", "nle_noalloc.cu"):
         o = os.path.join(BUILD, src.replace(".", "_") + ".o")
         cmds.append([nvcc, *NVFLAGS, "-c", os.path.join(CSRC, src), "-o", o])
         objs.append(o)

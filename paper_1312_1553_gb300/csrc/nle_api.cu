@@ -172,6 +172,11 @@ struct nle_ctx {
 
 static thread_local std::string g_create_error;
 
+namespace nle {
+// message for nle_last_error(NULL) from calls that take no handle
+void set_global_error(const std::string &msg) { g_create_error = msg; }
+}  // namespace nle
+
 static nle_status fail(nle_t h, nle_status code, const std::string &msg) {
   if (h)
     h->err = msg;

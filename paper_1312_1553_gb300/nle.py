@@ -28,7 +28,9 @@ NLE_MAX_P = 64
 
 # every symbol include/nle.h declares
 EXPORTS = ("nle_default_options", "nle_create", "nle_factor_ic", "nle_solve", "nle_backward", "nle_batch_solve",
-           "nle_apply_shifted", "nle_apply_prec", "nle_pcg", "nle_get_factor", "nle_last_error", "nle_destroy")
+           "nle_apply_shifted", "nle_apply_prec", "nle_pcg", "nle_get_factor", "nle_last_error", "nle_destroy",
+           "nle_ic_apply_noalloc")
+NLE_NOALLOC_MAX_N = 262144
 
 
 class nle_options(ctypes.Structure):
@@ -85,6 +87,7 @@ def load_library(path: str = LIB_PATH):
         "nle_get_factor": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
         "nle_last_error": (ctypes.c_char_p, [_vp]),
         "nle_destroy": (None, [_vp]),
+        "nle_ic_apply_noalloc": (ctypes.c_int, [_i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -158,6 +161,12 @@ def nle_get_factor(h, nnz_ptr, rp_ptr, col_ptr, val_ptr, levL_ptr, levU_ptr, nle
 
 def nle_destroy(h) -> None:
     load_library().nle_destroy(h)
+
+
+def nle_ic_apply_noalloc(n, Lrp_ptr, Lcol_ptr, Lval_ptr, Urp_ptr, Ucol_ptr, Uval_ptr, diag_ptr, g_ptr, c_ptr,
+                         stream_ptr) -> int:
+    return load_library().nle_ic_apply_noalloc(int(n), Lrp_ptr, Lcol_ptr, Lval_ptr, Urp_ptr, Ucol_ptr, Uval_ptr,
+                                               diag_ptr, g_ptr, c_ptr, stream_ptr)
 
 
 # ---- convenience wrapper with torch tensors --------------------------------
