@@ -153,10 +153,12 @@ struct nle_ctx {
   int vw = 4;
   int64_t npad = 0, nchunks = 0;
   int grid = 0, rpc = 0;
+  int64_t bsize = 0;
   int ldq = 0;
   // device memory
   DBuf d_perm, d_iperm;
-  DBuf A_sptr, A_col, A_val, A64_val, L_rp, L_col, L_val, U_rp, U_col, U_val, d_diag, d_pairdep;
+  DBuf A_sptr, A_col, A_val, A64_val, d_diag;
+  DBuf L_off, L_w, L_col, L_val, L_round, U_off, U_w, U_col, U_val, U_round;
   DBuf vecs;   // working-precision vectors
   DBuf vec64;  // Au, r, t
   DBuf dQ, dQt, dS, dR;
@@ -222,17 +224,21 @@ static Dev<T> make_dev(nle_t h) {
   D.npad = h->npad;
   D.nchunks = h->nchunks;
   D.ldq = h->ldq;
+  D.bsize = h->bsize;
   const int64_t ns = h->npad / (32 * h->vw);
   D.A = {ns, h->A_sptr.as<int64_t>(), h->A_col.as<int32_t>(), h->A_val.as<T>()};
   D.A64 = {ns, h->A_sptr.as<int64_t>(), h->A_col.as<int32_t>(), h->A64_val.as<double>()};
-  D.Lrp = h->L_rp.as<int32_t>();
+  D.Loff = h->L_off.as<int64_t>();
+  D.Lw = h->L_w.as<int32_t>();
   D.Lcol = h->L_col.as<int32_t>();
   D.Lval = h->L_val.as<T>();
-  D.Urp = h->U_rp.as<int32_t>();
+  D.Lround = h->L_round.as<uint8_t>();
+  D.Uoff = h->U_off.as<int64_t>();
+  D.Uw = h->U_w.as<int32_t>();
   D.Ucol = h->U_col.as<int32_t>();
   D.Uval = h->U_val.as<T>();
+  D.Uround = h->U_round.as<uint8_t>();
   D.diag = h->d_diag.as<T>();
-  D.pairdep = h->d_pairdep.as<uint8_t>();
   const int64_t np = h->npad, ext = h->npad + 32 * h->vw;
   T *v = h->vecs.as<T>();
   D.p = v + 0 * np;
@@ -282,13 +288,16 @@ template <typename T>
 static nle_status launch(nle_t h, int id, void **args) {
   void *fn = kernel_ptr<T>(id, h->rpc);
   if (!fn) return fail(h, NLE_ERR_ARG, "no kernel instance for this size");
+  // dynamic shared memory: the CTA's slab of the triangular solves
+  const size_t dyn = (size_t)h->bsize * (mixed(h) ? 4 : 8);
+  NLE_CUDA(h, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
   int nb = 0;
-  NLE_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, TPB, 0));
+  NLE_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, TPB, dyn));
   if (nb < 1 || h->grid > nb * h->nsm) return fail(h, NLE_ERR_CUDA, "persistent grid does not fit on the device");
   // reset the grid-barrier counter
   State *st = h->state.as<State>();
   NLE_CUDA(h, cudaMemsetAsync(&st->bar, 0, sizeof(unsigned), h->stream));
-  NLE_CUDA(h, cudaLaunchCooperativeKernel(fn, dim3(h->grid), dim3(TPB), args, 0, h->stream));
+  NLE_CUDA(h, cudaLaunchCooperativeKernel(fn, dim3(h->grid), dim3(TPB), args, dyn, h->stream));
   return NLE_OK;
 }
 
@@ -434,7 +443,6 @@ nle_status nle_factor_ic(nle_t h, int lfil, double tau_ic) {
   if (ic_factor_host(h->n, h->rowptr.data(), h->col.data(), h->val.data(), lfil, tau_ic, F, &bad) != 0)
     return fail(h, NLE_ERR_NOT_SPD, "non-positive pivot in IC column " + std::to_string(bad));
   h->F = std::move(F);
-  level_order(h->F, h->perm, h->iperm);
   const int H = 32 * h->vw;
   h->npad = ((h->n + H - 1) / H) * H;
   h->nchunks = h->npad / h->vw;
@@ -451,39 +459,51 @@ nle_status nle_factor_ic(nle_t h, int lfil, double tau_ic) {
   if (!rpc) return fail(h, NLE_ERR_ARG, "n too large for one persistent grid");
   h->grid = grid;
   h->rpc = rpc;
+  // one slab of rows per CTA in the triangular solves (a multiple of 4 rows,
+  // staged in shared memory)
+  h->bsize = ((h->npad + 4 * grid - 1) / (4 * grid)) * 4;
+  if (h->bsize * (int64_t)(mixed(h) ? 4 : 8) > 160 * 1024)
+    return fail(h, NLE_ERR_ARG, "n too large for the shared-memory slab of one persistent grid");
+  slab_level_order(h->F, h->bsize, h->perm, h->iperm);
   Permuted P;
   permute(h->n, h->rowptr.data(), h->col.data(), h->val.data(), h->F, h->perm, h->iperm, h->npad, P);
   const size_t tsz = mixed(h) ? 4 : 8;
   if (mixed(h)) {
     SellSet<float> S;
-    build_sell<float>(P, H, S);
+    build_sell<float>(P, H, h->bsize, S);
     NLE_CUDA(h, upload(h->A_sptr, S.A.sptr));
     NLE_CUDA(h, upload(h->A_col, S.A.col));
     NLE_CUDA(h, upload(h->A_val, S.A.val));
     NLE_CUDA(h, upload(h->A64_val, S.A64.val));
-    NLE_CUDA(h, upload(h->L_rp, S.L.rp));
+    NLE_CUDA(h, upload(h->L_off, S.L.off));
+    NLE_CUDA(h, upload(h->L_w, S.L.width));
     NLE_CUDA(h, upload(h->L_col, S.L.col));
     NLE_CUDA(h, upload(h->L_val, S.L.val));
-    NLE_CUDA(h, upload(h->U_rp, S.U.rp));
+    NLE_CUDA(h, upload(h->L_round, S.L.round));
+    NLE_CUDA(h, upload(h->U_off, S.U.off));
+    NLE_CUDA(h, upload(h->U_w, S.U.width));
     NLE_CUDA(h, upload(h->U_col, S.U.col));
     NLE_CUDA(h, upload(h->U_val, S.U.val));
+    NLE_CUDA(h, upload(h->U_round, S.U.round));
     NLE_CUDA(h, upload(h->d_diag, S.diag));
-    NLE_CUDA(h, upload(h->d_pairdep, S.pairdep));
   } else {
     SellSet<double> S;
-    build_sell<double>(P, H, S);
+    build_sell<double>(P, H, h->bsize, S);
     NLE_CUDA(h, upload(h->A_sptr, S.A.sptr));
     NLE_CUDA(h, upload(h->A_col, S.A.col));
     NLE_CUDA(h, upload(h->A_val, S.A.val));
     NLE_CUDA(h, upload(h->A64_val, S.A64.val));
-    NLE_CUDA(h, upload(h->L_rp, S.L.rp));
+    NLE_CUDA(h, upload(h->L_off, S.L.off));
+    NLE_CUDA(h, upload(h->L_w, S.L.width));
     NLE_CUDA(h, upload(h->L_col, S.L.col));
     NLE_CUDA(h, upload(h->L_val, S.L.val));
-    NLE_CUDA(h, upload(h->U_rp, S.U.rp));
+    NLE_CUDA(h, upload(h->L_round, S.L.round));
+    NLE_CUDA(h, upload(h->U_off, S.U.off));
+    NLE_CUDA(h, upload(h->U_w, S.U.width));
     NLE_CUDA(h, upload(h->U_col, S.U.col));
     NLE_CUDA(h, upload(h->U_val, S.U.val));
+    NLE_CUDA(h, upload(h->U_round, S.U.round));
     NLE_CUDA(h, upload(h->d_diag, S.diag));
-    NLE_CUDA(h, upload(h->d_pairdep, S.pairdep));
   }
   NLE_CUDA(h, upload(h->d_perm, h->perm));
   NLE_CUDA(h, upload(h->d_iperm, h->iperm));

@@ -350,76 +350,163 @@ __device__ __noinline__ T spin_value(const T *p, T v, State *st, long long spin_
   }
 }
 
-// Sync-free triangular solve over rows in level order (CSR of the strictly
-// triangular part, int32 row pointers, diagonal separate).  A warp works on
-// two consecutive rows at a time, 16 lanes per row, one matrix entry per
-// lane: every dependency of a row is fetched and, if not yet computed,
-// polled in parallel, so a row costs one L2 round trip once its inputs
-// exist.  Warps take row pairs round-robin in level order (ascending for L,
-// descending for L^T); the pair of a warp is only polled by later pairs.
-// When the second row of a pair depends on the first (pairdep[pair] = 1,
-// a level boundary), the two rows are done in two rounds separated by
-// __syncwarp, so no lane ever waits for a lane of its own warp.
+// Wait (bounded) for a value staged in this CTA's shared memory.
 template <typename T>
-struct TriRows {
-  const int32_t *rp;       // npad + 1
-  const int32_t *col;
+__device__ __noinline__ T spin_shared(const volatile T *p, State *st, long long spin_ns) {
+  const long long c0 = clock64();
+  const long long lim = spin_ns * 21 / 10;
+  T v = *p;
+  while (is_sent(v)) {
+    v = *p;
+    if (is_sent(v) && clock64() - c0 > lim) {
+      record_error(st, 8 /*NLE_ERR_TIMEOUT*/, 101);
+      return T(0);
+    }
+  }
+  return v;
+}
+
+// Sync-free triangular solve, one slab of rows per CTA.
+//
+// The unknowns are labelled slab-major, level-minor: CTA c owns positions
+// [c*bsize, (c+1)*bsize), which are a contiguous range of the natural row
+// order sorted by the level of each row in L.  A dependency inside the slab
+// is read from the CTA's shared-memory copy of the slab's results; one in
+// another slab (lower slabs for L, higher for L^T) is polled in global memory
+// with relaxed loads.  On the naturally ordered grids the solver meets, most
+// dependency chains stay inside a slab, so most hops cost a shared-memory
+// round trip instead of an L2 one.  Results start as a NaN payload that GPU
+// arithmetic never produces and are published both to shared and to global
+// memory; the value is its own ready flag.
+//
+// Each slab stores its rows in ELL form (width = the slab's longest row,
+// rounded up to 8), so the address of a row's entries follows from the row
+// index without a dependent load.  A warp takes four consecutive rows at a
+// time, 8 lanes per row, two entries per lane in flight, and fetches the
+// next group's entries, right-hand sides and diagonals before the current
+// group waits.  Rows of a group that depend on each other are done in
+// rounds (round[r] = longest chain to r inside its group, precomputed)
+// separated by __syncwarp, so a lane never waits for a lane of its own warp.
+// Every wait is bounded; since every warp and CTA is resident (cooperative
+// launch) and works in dependency order, every wait ends.
+template <typename T>
+struct TriEll {
+  const int64_t *off;    // per slab: first entry
+  const int32_t *width;  // per slab: entries per row (multiple of 8)
+  const int32_t *col;    // -1 = padding
   const T *val;
-  const T *diag;           // npad
-  const uint8_t *pairdep;  // npad / 2
+  const T *diag;          // npad
+  const uint8_t *round;   // npad: round of the row inside its group of 4
+};
+
+template <typename T>
+struct TriPre {
+  int c0, c1;
+  T a0, a1;
+  T rhs, dg;
+  int rnd;
 };
 
 template <bool LOWER, typename T, typename RHS>
-__device__ __forceinline__ void trsv_rows(const TriRows<T> &M, T *x, int64_t npad, int twarps, long long spin_ns,
-                                          int sleep_ns, State *st, RHS rhs_of) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (warp >= twarps) return;
-  const int64_t nw = (int64_t)gridDim.x * twarps;
-  const int64_t npair = npad >> 1;
-  const int q = lane >> 4, g = lane & 15;
-  for (int64_t it = (int64_t)blockIdx.x * twarps + warp; it < npair; it += nw) {
-    const int64_t pr = LOWER ? it : npair - 1 - it;
-    const int64_t r = 2 * pr + q;
-    const int e0 = __ldg(M.rp + r), e1 = __ldg(M.rp + r + 1);
-    const bool dep = __ldg(M.pairdep + pr) != 0;
-    // matrix entries of this lane (up to 3 without a loop; more in a loop)
-    int c0 = 0, c1 = 0, c2 = 0;
-    T a0 = T(0), a1 = T(0), a2 = T(0);
-    const int ea = e0 + g, eb = ea + 16, ec = eb + 16;
-    if (ea < e1) c0 = __ldg(M.col + ea), a0 = __ldg(M.val + ea);
-    if (eb < e1) c1 = __ldg(M.col + eb), a1 = __ldg(M.val + eb);
-    if (ec < e1) c2 = __ldg(M.col + ec), a2 = __ldg(M.val + ec);
-    T rhs = T(0), dg = T(1);
-    if (g == 0) {
-      rhs = rhs_of(r);
-      dg = __ldg(M.diag + r);
+__device__ __forceinline__ void trsv_fetch(const TriEll<T> &M, int64_t b0, int64_t base, int wd, int64_t ngrp,
+                                           int64_t it, int q, int g, RHS &rhs_of, TriPre<T> &P) {
+  const int64_t gi = LOWER ? it : ngrp - 1 - it;
+  const int64_t r = b0 + 4 * gi + q;
+  const int64_t e = base + (r - b0) * wd + g;
+  P.c0 = __ldg(M.col + e);
+  P.a0 = __ldg(M.val + e);
+  P.c1 = -1;
+  P.a1 = T(0);
+  if (g + 8 < wd) {
+    P.c1 = __ldg(M.col + e + 8);
+    P.a1 = __ldg(M.val + e + 8);
+  }
+  P.rnd = __ldg(M.round + r);
+  P.rhs = T(0);
+  P.dg = T(1);
+  if (g == 0) {
+    P.rhs = rhs_of(r);
+    P.dg = __ldg(M.diag + r);
+  }
+}
+
+// Value of dependency c: the shared copy inside the slab, global memory
+// outside.  The poll is inlined and checks no clock for its first 2^20
+// tries (a call per poll measurably slowed every dependency hop); after that
+// the bounded wait takes over.
+template <typename T>
+__device__ __forceinline__ T trsv_dep(const T *x, const volatile T *stage, int64_t b0, int64_t b1, int c, State *st,
+                                      long long spin_ns, int sleep_ns) {
+  if (c >= b0 && c < b1) {
+    T v = stage[c - b0];
+    for (int k = 0; is_sent(v); k++) {
+      if (k == (1 << 20)) return spin_shared(stage + (c - b0), st, spin_ns);
+      v = stage[c - b0];
     }
-    const int rounds = dep ? 2 : 1;
-    for (int rd = 0; rd < rounds; rd++) {
-      const bool active = !dep || (LOWER ? q == rd : q == 1 - rd);
-      T acc = T(0);
-      if (active) {
-        T x0 = T(0), x1 = T(0), x2 = T(0);
-        if (ea < e1) x0 = ld_relaxed(x + c0);
-        if (eb < e1) x1 = ld_relaxed(x + c1);
-        if (ec < e1) x2 = ld_relaxed(x + c2);
-        if (is_sent(x0)) x0 = spin_value(x + c0, x0, st, spin_ns, sleep_ns);
-        if (is_sent(x1)) x1 = spin_value(x + c1, x1, st, spin_ns, sleep_ns);
-        if (is_sent(x2)) x2 = spin_value(x + c2, x2, st, spin_ns, sleep_ns);
-        acc = a0 * x0 + a1 * x1 + a2 * x2;
-        for (int e = ec + 16; e < e1; e += 16) {
-          const int c = __ldg(M.col + e);
-          T xv = ld_relaxed(x + c);
-          if (is_sent(xv)) xv = spin_value(x + c, xv, st, spin_ns, sleep_ns);
-          acc += __ldg(M.val + e) * xv;
+    return v;
+  }
+  T v = ld_relaxed(x + c);
+  for (int k = 0; is_sent(v); k++) {
+    if (k == (1 << 20)) return spin_value(x + c, v, st, spin_ns, sleep_ns);
+    v = ld_relaxed(x + c);
+  }
+  return v;
+}
+
+template <bool LOWER, typename T, typename RHS>
+__device__ __forceinline__ void trsv_block(const TriEll<T> &M, T *x, int64_t npad, int64_t bsize, int twarps,
+                                           long long spin_ns, int sleep_ns, State *st, T *stage_mem, RHS rhs_of) {
+  const int64_t b0 = (int64_t)blockIdx.x * bsize;
+  const int64_t b1 = min(npad, b0 + bsize);
+  const int64_t nb = b1 > b0 ? b1 - b0 : 0;
+  volatile T *stage = stage_mem;
+  const T sent = sentinel<T>();
+  for (int64_t i = threadIdx.x; i < nb; i += blockDim.x) stage[i] = sent;
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t ngrp = nb >> 2;
+  int64_t it = warp;
+  if (warp < twarps && it < ngrp) {
+    const int q = lane >> 3, g = lane & 7;
+    const int64_t base = __ldg(M.off + blockIdx.x);
+    const int wd = __ldg(M.width + blockIdx.x);
+    TriPre<T> cur, nxt;
+    trsv_fetch<LOWER, T>(M, b0, base, wd, ngrp, it, q, g, rhs_of, cur);
+    for (;;) {
+      const int64_t itn = it + twarps;
+      const bool more = itn < ngrp;
+      // the next group's entries and right-hand sides load while this one waits
+      if (more) trsv_fetch<LOWER, T>(M, b0, base, wd, ngrp, itn, q, g, rhs_of, nxt);
+      const int64_t gi = LOWER ? it : ngrp - 1 - it;
+      const int64_t r = b0 + 4 * gi + q;
+      const int rounds = 1 + __reduce_max_sync(0xffffffffu, (unsigned)cur.rnd);
+      for (int rd = 0; rd < rounds; rd++) {
+        const bool active = (cur.rnd == rd);
+        T acc = T(0);
+        if (active) {
+          if (cur.c0 >= 0) acc = cur.a0 * trsv_dep(x, stage, b0, b1, cur.c0, st, spin_ns, sleep_ns);
+          if (cur.c1 >= 0) acc += cur.a1 * trsv_dep(x, stage, b0, b1, cur.c1, st, spin_ns, sleep_ns);
+          const int64_t e = base + (r - b0) * wd;
+          for (int k = g + 16; k < wd; k += 8) {
+            const int c = __ldg(M.col + e + k);
+            if (c >= 0) acc += __ldg(M.val + e + k) * trsv_dep(x, stage, b0, b1, c, st, spin_ns, sleep_ns);
+          }
         }
-      }
 #pragma unroll
-      for (int o = 8; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-      if (active && g == 0) st_relaxed(x + r, (rhs - acc) / dg);
-      if (dep) __syncwarp();
+        for (int o = 4; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (active && g == 0) {
+          const T v = (cur.rhs - acc) / cur.dg;
+          stage[r - b0] = v;
+          st_relaxed(x + r, v);
+        }
+        if (rounds > 1) __syncwarp();
+      }
+      if (!more) break;
+      it = itn;
+      cur = nxt;
     }
   }
+  __syncthreads();
 }
 
 }  // namespace nle

@@ -94,14 +94,17 @@ struct Dev {
   int64_t npad = 0;     // padded size (multiple of 32*VW)
   int64_t nchunks = 0;  // npad / VW
   int ldq = 0;          // allocated columns of Q / Qt
+  int64_t bsize = 0;    // rows per CTA slab in the triangular solves (multiple of 4)
   Sell<T> A;            // A in working precision
   Sell<double> A64;     // A in FP64 (same pattern and layout as A)
-  // strictly lower part of L and strictly upper part of U = L^T, level
-  // order, CSR with int32 row pointers (npad + 1), diagonal separate
-  const int32_t *Lrp = nullptr, *Lcol = nullptr, *Urp = nullptr, *Ucol = nullptr;
+  // strictly lower part of L and strictly upper part of U = L^T in the
+  // slab-major order, ELL per slab (offset and width per slab, col -1 =
+  // padding), diagonal separate, and the round of every row in its group of 4
+  const int64_t *Loff = nullptr, *Uoff = nullptr;
+  const int32_t *Lw = nullptr, *Uw = nullptr, *Lcol = nullptr, *Ucol = nullptr;
   const T *Lval = nullptr, *Uval = nullptr;
-  const T *diag = nullptr;           // diagonal of L (1 on padding rows)
-  const uint8_t *pairdep = nullptr;  // row 2i+1 depends on row 2i
+  const T *diag = nullptr;  // diagonal of L (1 on padding rows)
+  const uint8_t *Lround = nullptr, *Uround = nullptr;
   // working-precision vectors (npad; z and c0 have npad + 32*VW entries)
   T *p, *y, *s, *g, *z, *c0, *rT, *x, *Ax, *Ap;
   T *Q;        // npad * ldq, column c at Q + c*npad (converged v_1.. and u)

@@ -211,25 +211,31 @@ __device__ bool gram(const Dev<T> &D, Shared &sh, Ctl &ctl, int m, int k) {
 // use_beta).  On entry z/c0 hold the not-yet-computed marker and the solve
 // queues are reset.  *gamma_new receives gamma' = g^T c.
 //
-// The triangular solves run on ctl.twarps warps per CTA (trsv_rows): every
-// row pair is taken after all lower pairs (higher, for L^T) by resident
-// warps, so every wait ends (co-residency comes from the cooperative launch).
+// The triangular solves (trsv_block) work slab by slab, one slab per CTA,
+// with ctl.twarps warps of the CTA taking the slab's row pairs in order.
 // ---------------------------------------------------------------------------
-template <typename T>
-__device__ __forceinline__ void trsv_forward(const Dev<T> &D, Shared &sh, const Ctl &ctl, int k) {
-  const TriRows<T> L{D.Lrp, D.Lcol, D.Lval, D.diag, D.pairdep};
-  trsv_rows<true, T>(L, D.z, D.npad, ctl.twarps, ctl.spin_ns, ctl.sleep_ns, D.st, [&](int64_t r) {
-    T w = __ldcg(D.g + r);
-    for (int t = 0; t < k; t++) w -= T(sh.a[t]) * __ldcg(D.R + (int64_t)sh.order[t] * D.npad + r);
-    return w;
-  });
-}
+extern __shared__ __align__(16) unsigned char nle_dyn_smem[];  // slab of the triangular solves
 
 template <typename T>
+__device__ __forceinline__ void trsv_forward(const Dev<T> &D, Shared &sh, const Ctl &ctl, int k) {
+  const TriEll<T> L{D.Loff, D.Lw, D.Lcol, D.Lval, D.diag, D.Lround};
+  trsv_block<true, T>(L, D.z, D.npad, D.bsize, ctl.twarps, ctl.spin_ns, ctl.sleep_ns, D.st,
+                      reinterpret_cast<T *>(nle_dyn_smem), [&](int64_t r) {
+                        T w = __ldcg(D.g + r);
+                        for (int t = 0; t < k; t++)
+                          w -= T(sh.a[t]) * __ldcg(D.R + (int64_t)sh.order[t] * D.npad + r);
+                        return w;
+                      });
+}
+
+// The right-hand side of the backward solve is the forward result of the
+// CTA's own slab, complete after trsv_forward's closing __syncthreads, so no
+// grid barrier separates the two solves.
+template <typename T>
 __device__ __forceinline__ void trsv_backward(const Dev<T> &D, const Ctl &ctl) {
-  const TriRows<T> U{D.Urp, D.Ucol, D.Uval, D.diag, D.pairdep};
-  trsv_rows<false, T>(U, D.c0, D.npad, ctl.twarps, ctl.spin_ns, ctl.sleep_ns, D.st,
-                      [&](int64_t r) { return __ldcg(D.z + r); });
+  const TriEll<T> U{D.Uoff, D.Uw, D.Ucol, D.Uval, D.diag, D.Uround};
+  trsv_block<false, T>(U, D.c0, D.npad, D.bsize, ctl.twarps, ctl.spin_ns, ctl.sleep_ns, D.st,
+                       reinterpret_cast<T *>(nle_dyn_smem), [&](int64_t r) { return __ldcg(D.z + r); });
 }
 
 template <typename T>
@@ -246,7 +252,6 @@ __device__ bool precond_tail(const Dev<T> &D, Shared &sh, Ctl &ctl, int m, int k
   constexpr int W = VT<T>::W;
   const int64_t tid = gtid(), TT = gthreads();
   trsv_forward<T>(D, sh, ctl, k);
-  if (!grid_sync(D.st, sh, ctl, 20)) return false;
   tmark(sh, PH_FWD);
   trsv_backward<T>(D, ctl);
   if (!grid_sync(D.st, sh, ctl, 21)) return false;

@@ -226,18 +226,20 @@ int ic_factor_host(int64_t n, const int64_t *rp, const int32_t *ci, const double
   return 0;
 }
 
-void level_order(const Factor &F, std::vector<int32_t> &perm, std::vector<int32_t> &iperm) {
+void slab_level_order(const Factor &F, int64_t bsize, std::vector<int32_t> &perm, std::vector<int32_t> &iperm) {
   const int64_t n = F.n;
-  std::vector<int64_t> ptr(F.nlevL + 1, 0);
-  for (int64_t i = 0; i < n; i++) ptr[F.levL[i] + 1]++;
-  for (int64_t l = 0; l < F.nlevL; l++) ptr[l + 1] += ptr[l];
-  perm.assign(n, 0);
+  perm.resize(n);
+  for (int64_t i = 0; i < n; i++) perm[i] = (int32_t)i;
+  // slabs are contiguous ranges of the natural order, so sorting by
+  // (slab, level, row) keeps every row inside its slab
+  std::sort(perm.begin(), perm.end(), [&](int32_t a, int32_t b) {
+    const int64_t sa = a / bsize, sb = b / bsize;
+    if (sa != sb) return sa < sb;
+    if (F.levL[a] != F.levL[b]) return F.levL[a] < F.levL[b];
+    return a < b;
+  });
   iperm.assign(n, 0);
-  for (int64_t i = 0; i < n; i++) {
-    const int64_t p = ptr[F.levL[i]]++;
-    perm[p] = (int32_t)i;
-    iperm[i] = (int32_t)p;
-  }
+  for (int64_t p = 0; p < n; p++) iperm[perm[p]] = (int32_t)p;
 }
 
 // Pack rows of a matrix given row by row (in new numbering) into SELL.
@@ -274,33 +276,61 @@ static void pack(int64_t n, int64_t npad, int H, const std::vector<int64_t> &rp,
   }
 }
 
+// Per-slab ELL of a strictly triangular matrix given by rows (relabelled
+// order), plus the round of every row inside its group of 4 rows: the length
+// of the longest dependency chain ending at the row within the group
+// (lower: earlier rows of the group; upper: later rows).
 template <typename TV>
-static void tri(int64_t n, int64_t npad, const std::vector<int64_t> &rp, const std::vector<int32_t> &col,
-                const std::vector<double> &val, TriHost<TV> &out) {
-  out.rp.assign(npad + 1, 0);
-  for (int64_t i = 0; i <= npad; i++) out.rp[i] = (int32_t)rp[std::min(i, n)];
-  out.col.assign(col.begin(), col.end());
-  out.val.resize(val.size());
-  for (size_t e = 0; e < val.size(); e++) out.val[e] = TV(val[e]);
+static void ell(int64_t n, int64_t npad, int64_t bsize, bool lower, const std::vector<int64_t> &rp,
+                const std::vector<int32_t> &col, const std::vector<double> &val, EllHost<TV> &out) {
+  const int64_t ns = (npad + bsize - 1) / bsize;
+  out.off.assign(ns + 1, 0);
+  out.width.assign(ns, 8);
+  for (int64_t s = 0; s < ns; s++) {
+    int64_t w = 0;
+    for (int64_t r = s * bsize; r < std::min(n, (s + 1) * bsize); r++) w = std::max(w, rp[r + 1] - rp[r]);
+    w = std::max<int64_t>(8, (w + 7) / 8 * 8);
+    out.width[s] = (int32_t)w;
+    const int64_t rows = std::min(npad, (s + 1) * bsize) - s * bsize;
+    out.off[s + 1] = out.off[s] + rows * w;
+  }
+  out.col.assign(out.off[ns], -1);
+  out.val.assign(out.off[ns], TV(0));
+  for (int64_t s = 0; s < ns; s++)
+    for (int64_t r = s * bsize; r < std::min(n, (s + 1) * bsize); r++) {
+      const int64_t base = out.off[s] + (r - s * bsize) * out.width[s];
+      for (int64_t e = rp[r]; e < rp[r + 1]; e++) {
+        out.col[base + (e - rp[r])] = col[e];
+        out.val[base + (e - rp[r])] = TV(val[e]);
+      }
+    }
+  out.round.assign(npad, 0);
+  for (int64_t g0 = 0; g0 < n; g0 += 4) {
+    const int64_t g1 = std::min(n, g0 + 4);
+    if (lower) {
+      for (int64_t r = g0; r < g1; r++)
+        for (int64_t e = rp[r]; e < rp[r + 1]; e++)
+          if (col[e] >= g0) out.round[r] = std::max<uint8_t>(out.round[r], out.round[col[e]] + 1);
+    } else {
+      for (int64_t r = g1 - 1; r >= g0; r--)
+        for (int64_t e = rp[r]; e < rp[r + 1]; e++)
+          if (col[e] < g1) out.round[r] = std::max<uint8_t>(out.round[r], out.round[col[e]] + 1);
+    }
+  }
 }
 
 template <typename TV>
-void build_sell(const Permuted &P, int H, SellSet<TV> &S) {
+void build_sell(const Permuted &P, int H, int64_t bsize, SellSet<TV> &S) {
   pack<TV>(P.n, P.npad, H, P.Arp, P.Acol, P.Aval, 0, 0, S.A);
   pack<double>(P.n, P.npad, H, P.Arp, P.Acol, P.Aval, 0, 0, S.A64);
-  tri<TV>(P.n, P.npad, P.Lrp, P.Lcol, P.Lval, S.L);
-  tri<TV>(P.n, P.npad, P.Urp, P.Ucol, P.Uval, S.U);
+  ell<TV>(P.n, P.npad, bsize, true, P.Lrp, P.Lcol, P.Lval, S.L);
+  ell<TV>(P.n, P.npad, bsize, false, P.Urp, P.Ucol, P.Uval, S.U);
   S.diag.assign(P.npad, TV(1));
   for (int64_t i = 0; i < P.n; i++) S.diag[i] = TV(P.diag[i]);
-  // a pair of rows (2i, 2i+1) is coupled when L'(2i+1, 2i) != 0
-  S.pairdep.assign(P.npad / 2, 0);
-  for (int64_t i = 1; i < P.n; i += 2)
-    for (int64_t e = P.Lrp[i]; e < P.Lrp[i + 1]; e++)
-      if (P.Lcol[e] == i - 1) S.pairdep[i / 2] = 1;
 }
 
-template void build_sell<float>(const Permuted &, int, SellSet<float> &);
-template void build_sell<double>(const Permuted &, int, SellSet<double> &);
+template void build_sell<float>(const Permuted &, int, int64_t, SellSet<float> &);
+template void build_sell<double>(const Permuted &, int, int64_t, SellSet<double> &);
 
 void permute(int64_t n, const int64_t *rp, const int32_t *ci, const double *va, const Factor &F,
              const std::vector<int32_t> &perm, const std::vector<int32_t> &iperm, int64_t npad, Permuted &P) {

@@ -37,20 +37,22 @@ struct SellHost {
   std::vector<TV> val;
 };
 
+// Strictly triangular part in per-slab ELL form (see trsv_block).
 template <typename TV>
-struct TriHost {
-  std::vector<int32_t> rp;  // npad + 1
-  std::vector<int32_t> col;
+struct EllHost {
+  std::vector<int64_t> off;    // per slab: first entry
+  std::vector<int32_t> width;  // per slab: entries per row, multiple of 8
+  std::vector<int32_t> col;    // -1 = padding
   std::vector<TV> val;
+  std::vector<uint8_t> round;  // per row: longest chain to it inside its group of 4
 };
 
 template <typename TV>
 struct SellSet {
   SellHost<TV> A;
   SellHost<double> A64;
-  TriHost<TV> L, U;            // strictly lower / upper parts, level order
-  std::vector<TV> diag;        // npad, 1 on padding rows
-  std::vector<uint8_t> pairdep;  // npad / 2: row 2i+1 depends on row 2i
+  EllHost<TV> L, U;      // strictly lower / upper parts, slab-major order
+  std::vector<TV> diag;  // npad, 1 on padding rows
 };
 
 // 0 on success; 2 = malformed CSR, 3 = non-positive diagonal (msg says why).
@@ -61,13 +63,15 @@ int validate_csr(int64_t n, int64_t nnz, const int64_t *rp, const int32_t *ci, c
 int ic_factor_host(int64_t n, const int64_t *rp, const int32_t *ci, const double *va, int lfil, double tau,
                    Factor &F, int64_t *bad_col);
 
-// perm[new] = old: rows level by level (ascending row inside a level).
-void level_order(const Factor &F, std::vector<int32_t> &perm, std::vector<int32_t> &iperm);
+// perm[new] = old: rows cut into slabs of bsize consecutive rows of the
+// natural order; inside a slab, by level of L, then by row.  Every slab keeps
+// its position range, and P L P^T stays lower triangular.
+void slab_level_order(const Factor &F, int64_t bsize, std::vector<int32_t> &perm, std::vector<int32_t> &iperm);
 
 void permute(int64_t n, const int64_t *rp, const int32_t *ci, const double *va, const Factor &F,
              const std::vector<int32_t> &perm, const std::vector<int32_t> &iperm, int64_t npad, Permuted &P);
 
 template <typename TV>
-void build_sell(const Permuted &P, int H, SellSet<TV> &S);
+void build_sell(const Permuted &P, int H, int64_t bsize, SellSet<TV> &S);
 
 }  // namespace nle
