@@ -26,7 +26,7 @@ void *kernel_ptr_d1(int);
 void *kernel_ptr_d2(int);
 void *kernel_ptr_d4(int);
 void *kernel_ptr_d8(int);
-enum KernelId { K_NEWTON = 0, K_DACG = 1, K_SHIFTED = 2, K_PREC = 3, K_PCG = 4 };
+enum KernelId { K_NEWTON = 0, K_DACG = 1, K_SHIFTED = 2, K_PREC = 3, K_PCG = 4, K_ADJOINT = 5 };
 template <typename T>
 void *kernel_ptr(int id, int rpc);
 template <>
@@ -67,7 +67,8 @@ __global__ void k_scatter(double *dst, const T *src, const int32_t *iperm, int64
 }
 // V[j*n + o] = sgn_j * Qt[j*npad + iperm[o]], sgn_j making the entry of
 // largest modulus positive (lowest natural index on ties).  One block per j.
-__global__ void k_output_vectors(double *V, const double *Qt, const int32_t *iperm, int64_t n, int64_t npad) {
+__global__ void k_output_vectors(double *V, const double *Qt, const int32_t *iperm, int64_t n, int64_t npad,
+                                 State *st) {
   const int j = blockIdx.x;
   const double *q = Qt + (int64_t)j * npad;
   double best = -1.0;
@@ -90,7 +91,31 @@ __global__ void k_output_vectors(double *V, const double *Qt, const int32_t *ipe
     __syncthreads();
   }
   const double sgn = (q[iperm[si[0]]] < 0.0) ? -1.0 : 1.0;
+  if (threadIdx.x == 0) st->sign[j] = sgn;
   for (int64_t o = threadIdx.x; o < n; o += blockDim.x) V[(int64_t)j * n + o] = sgn * q[iperm[o]];
+}
+// dst[i] = sign_j * src[perm[i]] (FP64, level order), 0 on padding
+__global__ void k_gather_signed(double *dst, const double *src, const int32_t *perm, int64_t n, int64_t npad,
+                                const State *st, int j) {
+  const double sg = st->sign[j];
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < npad; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = (i < n) ? sg * src[perm[i]] : 0.0;
+}
+// grad[e] += sum_j gl[j] v_j[a] v_j[b] for every stored entry e = (a, b)
+__global__ void k_grad_lambda(double *grad, const int32_t *erow, const int32_t *ecol, int64_t nnz,
+                              const int32_t *iperm, const double *Qt, int64_t npad, int p, const double *gl) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t a = iperm[erow[e]], b = iperm[ecol[e]];
+    double acc = 0.0;
+    for (int j = 0; j < p; j++) acc += gl[j] * Qt[(int64_t)j * npad + a] * Qt[(int64_t)j * npad + b];
+    grad[e] += acc;
+  }
+}
+// grad[e] += xi[a] v_j[b]
+__global__ void k_grad_vec(double *grad, const int32_t *erow, const int32_t *ecol, int64_t nnz, const int32_t *iperm,
+                           const double *xi, const double *vj) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x)
+    grad[e] += xi[iperm[erow[e]]] * vj[iperm[ecol[e]]];
 }
 __global__ void k_set_j(State *st, int j) {
   st->j = j;
@@ -164,6 +189,7 @@ struct nle_ctx {
   DBuf dQ, dQt, dS, dR;
   DBuf part, state;
   DBuf scratch;  // 2 * n doubles for host transfers
+  DBuf d_erow, d_ecol, d_grad;  // natural-order entries (adjoint)
   std::vector<double> pinned_dummy;
   bool solved = false;
   int last_p = 0;
@@ -255,6 +281,8 @@ static Dev<T> make_dev(nle_t h) {
   D.Au = w;
   D.r = w + np;
   D.t = w + 2 * np;
+  D.y64 = w + 3 * np;
+  D.b64 = w + 4 * np;
   D.u = nullptr;
   D.Q = h->dQ.as<T>();
   D.Qt = h->dQt.as<double>();
@@ -509,7 +537,7 @@ nle_status nle_factor_ic(nle_t h, int lfil, double tau_ic) {
   NLE_CUDA(h, upload(h->d_iperm, h->iperm));
   const int64_t ext = h->npad + 32 * h->vw;
   NLE_CUDA(h, dalloc(h->vecs, (size_t)(8 * h->npad + 2 * ext) * tsz));
-  NLE_CUDA(h, dalloc(h->vec64, (size_t)3 * h->npad * 8));
+  NLE_CUDA(h, dalloc(h->vec64, (size_t)5 * h->npad * 8));
   NLE_CUDA(h, dalloc(h->dS, (size_t)h->npad * KMAX * tsz));
   NLE_CUDA(h, dalloc(h->dR, (size_t)h->npad * KMAX * tsz));
   NLE_CUDA(h, dalloc(h->part, (size_t)2 * RED_MAX * h->grid * 8));
@@ -591,7 +619,7 @@ static nle_status solve_impl(nle_t h, int p, double tol, int max_newton, int max
     NLE_CUDA(h, dalloc(tmp, (size_t)p * h->n * 8));
     vout = tmp.as<double>();
   }
-  k_output_vectors<<<p, 1024, 0, h->stream>>>(vout, D.Qt, h->d_iperm.as<int32_t>(), h->n, h->npad);
+  k_output_vectors<<<p, 1024, 0, h->stream>>>(vout, D.Qt, h->d_iperm.as<int32_t>(), h->n, h->npad, D.st);
   launches++;
   NLE_CUDA(h, cudaGetLastError());
   if (!on_dev) NLE_CUDA(h, cudaMemcpyAsync(V, vout, (size_t)p * h->n * 8, cudaMemcpyDeviceToHost, h->stream));
@@ -702,6 +730,7 @@ extern "C" nle_status nle_apply_prec(nle_t h, int k, const double *S, const doub
   if (k < 0 || k > NLE_MAX_KMAX || m < 0 || m > NLE_MAX_P || !g || !c || (k > 0 && (!S || !R)) || (m > 0 && !Q))
     return fail(h, NLE_ERR_ARG, "bad nle_apply_prec arguments");
   cudaSetDevice(h->device);
+  h->solved = false;  // overwrites the stored eigenvectors
   return mixed(h) ? prec_impl<float>(h, k, S, R, m, Q, g, c, buffers_on_device)
                   : prec_impl<double>(h, k, S, R, m, Q, g, c, buffers_on_device);
 }
@@ -746,19 +775,82 @@ extern "C" nle_status nle_pcg(nle_t h, double theta, double tol, int max_pcg, co
       (k > 0 && (!S || !R)))
     return fail(h, NLE_ERR_ARG, "bad nle_pcg arguments");
   cudaSetDevice(h->device);
+  h->solved = false;  // overwrites the stored eigenvectors
   return mixed(h) ? pcg_impl<float>(h, theta, tol, max_pcg, r, m, Q, k, S, R, s, info, buffers_on_device)
                   : pcg_impl<double>(h, theta, tol, max_pcg, r, m, Q, k, S, R, s, info, buffers_on_device);
+}
+
+template <typename T>
+static nle_status backward_impl(nle_t h, const double *gl, const double *gV, double *grad_val, int on_dev) {
+  const int p = h->last_p;
+  const int64_t n = h->n, nnz = h->nnz;
+  for (int i = 0; i < p; i++)
+    for (int j = i + 1; j < p; j++)
+      if (std::fabs(h->lambda[i] - h->lambda[j]) <= 1e-12 * std::fabs(h->lambda[j]))
+        return fail(h, NLE_ERR_ARG, "repeated eigenvalue: the eigenvector adjoint is undefined");
+  if (!h->d_erow.p) {
+    std::vector<int32_t> er(nnz);
+    for (int64_t i = 0; i < n; i++)
+      for (int64_t e = h->rowptr[i]; e < h->rowptr[i + 1]; e++) er[e] = (int32_t)i;
+    NLE_CUDA(h, upload(h->d_erow, er));
+    NLE_CUDA(h, upload(h->d_ecol, h->col));
+  }
+  double *grad = grad_val;
+  if (!on_dev) {
+    NLE_CUDA(h, dalloc(h->d_grad, (size_t)nnz * 8));
+    NLE_CUDA(h, cudaMemcpyAsync(h->d_grad.p, grad_val, nnz * 8, cudaMemcpyHostToDevice, h->stream));
+    grad = h->d_grad.as<double>();
+  }
+  Dev<T> D = make_dev<T>(h);
+  const int32_t *erow = h->d_erow.as<int32_t>(), *ecol = h->d_ecol.as<int32_t>();
+  const int32_t *iperm = h->d_iperm.as<int32_t>(), *perm = h->d_perm.as<int32_t>();
+  if (gl) {
+    const double *gld = gl;
+    if (!on_dev) {
+      NLE_CUDA(h, cudaMemcpyAsync(h->scratch.p, gl, p * 8, cudaMemcpyHostToDevice, h->stream));
+      gld = h->scratch.as<double>();
+    }
+    k_grad_lambda<<<1024, 256, 0, h->stream>>>(grad, erow, ecol, nnz, iperm, D.Qt, h->npad, p, gld);
+    NLE_CUDA(h, cudaGetLastError());
+  }
+  if (gV) {
+    // inner solves: exits (iii)/(iv) off, relative tolerance per correction
+    Opts O = make_opts(h, 1e-8, 1, 2000);
+    O.tau_pcg = mixed(h) ? 1e-3 : 1e-6;
+    O.exit_eigres = 0;
+    O.exit_stag = 0;
+    double tol = 1e-10;
+    int max_refine = 40;
+    for (int j = 0; j < p; j++) {
+      const double *src = gV + (int64_t)j * n;
+      if (!on_dev) {
+        NLE_CUDA(h, cudaMemcpyAsync(h->scratch.p, src, n * 8, cudaMemcpyHostToDevice, h->stream));
+        src = h->scratch.as<double>();
+      }
+      k_gather_signed<<<1024, 256, 0, h->stream>>>(D.b64, src, perm, n, h->npad, D.st, j);
+      NLE_CUDA(h, cudaGetLastError());
+      int jj = j, pp = p;
+      void *args[] = {&D, &O, &jj, &pp, &tol, &max_refine};
+      nle_status s = launch<T>(h, K_ADJOINT, args);
+      if (s != NLE_OK) return s;
+      if ((s = check_state_error(h)) != NLE_OK) return s;
+      k_grad_vec<<<1024, 256, 0, h->stream>>>(grad, erow, ecol, nnz, iperm, D.t, D.Qt + (int64_t)j * h->npad);
+      NLE_CUDA(h, cudaGetLastError());
+    }
+  }
+  if (!on_dev) NLE_CUDA(h, cudaMemcpyAsync(grad_val, grad, nnz * 8, cudaMemcpyDeviceToHost, h->stream));
+  NLE_CUDA(h, cudaStreamSynchronize(h->stream));
+  return NLE_OK;
 }
 
 extern "C" nle_status nle_backward(nle_t h, const double *gbar_lambda, const double *gbar_V, double *grad_val,
                                    int buffers_on_device) {
   if (!h) return fail(nullptr, NLE_ERR_ARG, "NULL handle");
   if (!h->solved) return fail(h, NLE_ERR_STATE, "nle_solve has not completed");
-  (void)gbar_lambda;
-  (void)gbar_V;
-  (void)grad_val;
-  (void)buffers_on_device;
-  return fail(h, NLE_ERR_STATE, "nle_backward is not available in this build");
+  if (!grad_val) return fail(h, NLE_ERR_ARG, "grad_val is NULL");
+  cudaSetDevice(h->device);
+  return mixed(h) ? backward_impl<float>(h, gbar_lambda, gbar_V, grad_val, buffers_on_device)
+                  : backward_impl<double>(h, gbar_lambda, gbar_V, grad_val, buffers_on_device);
 }
 
 extern "C" nle_status nle_batch_solve(int count, nle_t *hs, int p, double tol, int max_newton, int max_pcg,

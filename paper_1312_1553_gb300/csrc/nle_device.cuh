@@ -144,6 +144,7 @@ struct Shared {
   double gqs[MMAX][KMAX];      // q_c^T s_t
   double zq[MMAX];             // Q^T c (Algorithm 3.1, last two steps)
   double qv[MMAX];             // Q^T v of the current projection
+  double cadj[MMAX];           // adjoint: v_i^T gbar
   int order[KMAX];             // chronological -> physical pair slot
   int ok;                      // error word broadcast after each barrier
   long long tlast;             // phase timer (CTA 0, thread 0)

@@ -60,6 +60,9 @@ struct State {
   long long dacg_sum_m;  // sum over DACG iterations of the deflated columns
   long long dacg_total;  // DACG iterations
   int exits[5];
+  double sign[MMAX];  // sign applied to each output eigenvector (largest entry positive)
+  int adj_refine, adj_inner;  // refinement steps and inner iterations of the last adjoint solve
+  double adj_res;             // its final relative FP64 residual
   // last single inner solve (nle_pcg)
   int last_its, last_exit;
   double last_g0, last_gn, last_eres;
@@ -111,6 +114,7 @@ struct Dev {
   T *S, *R;    // npad * KMAX, BFGS pairs by physical slot
   // FP64 vectors
   double *u, *Au, *r, *t;
+  double *y64, *b64;  // adjoint solve: solution and right-hand side
   double *Qt;  // npad * ldq, FP64 converged eigenvectors
   // reductions / control
   double *part;  // 2 * RED_MAX * gridDim

@@ -1088,6 +1088,217 @@ __global__ void __launch_bounds__(TPB, 1) k_pcg(Dev<T> D, Opts O, int m, int k, 
 }
 
 // ---------------------------------------------------------------------------
+// Kernel: adjoint solve for eigenvector j (not in the paper).
+// On entry b64 holds gbar_j (level order, FP64, already multiplied by the
+// sign of the output eigenvector); Qt holds v_1..v_p (FP64) and Q their
+// working-precision shadows; st->lambda the eigenvalues.  Computes
+//   c_i = v_i^T gbar,   b = gbar - V c,
+//   y perp V solving (I-VV^T)(A - lambda_j I)(I-VV^T) y = b,
+//   xi = -sum_{i != j} v_i c_i / (lambda_i - lambda_j) - y   (written to t),
+// the solve by iterative refinement: FP64 residual rho = b - (I-VV^T)(A -
+// lambda_j I) y with the FP64 matrix, correction by the inner projected PCG
+// of the correction equation (Q = V, IC preconditioner, shift lambda_j) in the
+// working precision, until ||rho|| <= tol ||b||.
+// ---------------------------------------------------------------------------
+template <typename T, int RPC>
+__device__ bool fp64_project_dots(const Dev<T> &D, Shared &sh, Ctl &ctl, int p, const double (&v)[RPC][VT<T>::W],
+                                  int where) {
+  constexpr int W = VT<T>::W;
+  const int64_t tid = gtid(), TT = gthreads();
+  int c = 0;
+  for (; c < p; c++) {
+    const double *qc = D.Qt + (int64_t)c * D.npad;
+    double acc = 0.0;
+#pragma unroll
+    for (int i = 0; i < RPC; i++) {
+      const int64_t ch = tid + i * TT;
+      if (ch < D.nchunks) {
+        double q[W];
+        ldc(qc + ch * W, q);
+#pragma unroll
+        for (int u = 0; u < W; u++) acc += q[u] * v[i][u];
+      }
+    }
+    red_put(sh, c, acc);
+  }
+  return reduce_all(D, sh, ctl, p, where);
+}
+
+template <typename T, int RPC>
+__device__ void fp64_comb_add(const Dev<T> &D, int p, const double *coef, double sgn, double (&v)[RPC][VT<T>::W]) {
+  constexpr int W = VT<T>::W;
+  const int64_t tid = gtid(), TT = gthreads();
+  for (int c = 0; c < p; c++) {
+    const double *qc = D.Qt + (int64_t)c * D.npad;
+    const double cf = sgn * coef[c];
+#pragma unroll
+    for (int i = 0; i < RPC; i++) {
+      const int64_t ch = tid + i * TT;
+      if (ch < D.nchunks) {
+        double q[W];
+        ldc(qc + ch * W, q);
+#pragma unroll
+        for (int u = 0; u < W; u++) v[i][u] += cf * q[u];
+      }
+    }
+  }
+}
+
+template <typename T, int RPC>
+__global__ void __launch_bounds__(TPB, 1) k_adjoint(Dev<T> D, Opts O, int j, int p, double tol, int max_refine) {
+  constexpr int W = VT<T>::W;
+  __shared__ Shared sh;
+  Ctl ctl;
+  load_state(D, sh, ctl, O);
+  const int64_t tid = gtid(), TT = gthreads();
+  const double lam = D.st->lambda[j];
+  double v[RPC][W];
+  // 1-2: c = V^T gbar, b = gbar - V c, y = 0
+#pragma unroll
+  for (int i = 0; i < RPC; i++) {
+    const int64_t ch = tid + i * TT;
+    if (ch < D.nchunks)
+      ldc(D.b64 + ch * W, v[i]);
+    else
+#pragma unroll
+      for (int u = 0; u < W; u++) v[i][u] = 0.0;
+  }
+  if (!fp64_project_dots<T, RPC>(D, sh, ctl, p, v, 70)) return;
+  for (int c = threadIdx.x; c < p; c += TPB) sh.cadj[c] = sh.sc[c];
+  __syncthreads();
+  fp64_comb_add<T, RPC>(D, p, sh.cadj, -1.0, v);
+  {
+    double bb = 0.0;
+    const double zero[W] = {};
+#pragma unroll
+    for (int i = 0; i < RPC; i++) {
+      const int64_t ch = tid + i * TT;
+      if (ch < D.nchunks) {
+        stv(D.b64 + ch * W, v[i]);
+        double zz[W];
+#pragma unroll
+        for (int u = 0; u < W; u++) zz[u] = zero[u];
+        stv(D.y64 + ch * W, zz);
+#pragma unroll
+        for (int u = 0; u < W; u++) bb += v[i][u] * v[i][u];
+      }
+    }
+    red_put(sh, 0, bb);
+    if (!reduce_all(D, sh, ctl, 1, 71)) return;
+  }
+  const double bn = sqrt(sh.sc[0]);
+  int refine = 0, inner = 0;
+  double res = 0.0;
+  for (int it = 0; bn > 0.0 && it < max_refine; it++) {
+    // a: w = (A - lambda I) y in FP64, V^T w
+    double w[RPC][W];
+#pragma unroll
+    for (int i = 0; i < RPC; i++) {
+      const int64_t ch = tid + i * TT;
+      if (ch < D.nchunks) {
+        double acc[W], yy[W];
+        sell_rows<W, double, double, double>(D.A64, D.y64, ch, acc);
+        ldc(D.y64 + ch * W, yy);
+#pragma unroll
+        for (int u = 0; u < W; u++) w[i][u] = acc[u] - lam * yy[u];
+      } else {
+#pragma unroll
+        for (int u = 0; u < W; u++) w[i][u] = 0.0;
+      }
+    }
+    if (!fp64_project_dots<T, RPC>(D, sh, ctl, p, w, 72)) return;
+    for (int c = threadIdx.x; c < p; c += TPB) sh.qv[c] = sh.sc[c];
+    __syncthreads();
+    fp64_comb_add<T, RPC>(D, p, sh.qv, -1.0, w);  // w = (I - VV^T)(A - lambda I) y
+    // b: rho = b - w, ||rho||, rT = -rho
+    {
+      double rr = 0.0;
+#pragma unroll
+      for (int i = 0; i < RPC; i++) {
+        const int64_t ch = tid + i * TT;
+        if (ch < D.nchunks) {
+          double bv[W];
+          T rt[W];
+          ldc(D.b64 + ch * W, bv);
+#pragma unroll
+          for (int u = 0; u < W; u++) {
+            const double rho = bv[u] - w[i][u];
+            rr += rho * rho;
+            rt[u] = T(-rho);
+          }
+          stv(D.rT + ch * W, rt);
+        }
+      }
+      red_put(sh, 0, rr);
+      if (!reduce_all(D, sh, ctl, 1, 73)) return;
+    }
+    res = sqrt(sh.sc[0]) / bn;
+    if (res <= tol) break;
+    // d: correction by the inner projected PCG (J s = rho)
+    PcgOut po;
+    if (!pcg_solve<T, RPC>(D, O, sh, ctl, p, 0, lam, O.max_pcg, po)) return;
+    inner += po.its;
+    refine++;
+    // e: y += s, then y -= V V^T y
+    double yv[RPC][W];
+#pragma unroll
+    for (int i = 0; i < RPC; i++) {
+      const int64_t ch = tid + i * TT;
+      if (ch < D.nchunks) {
+        T sv[W];
+        ldc(D.y64 + ch * W, yv[i]);
+        ldc(D.s + ch * W, sv);
+#pragma unroll
+        for (int u = 0; u < W; u++) yv[i][u] += double(sv[u]);
+      } else {
+#pragma unroll
+        for (int u = 0; u < W; u++) yv[i][u] = 0.0;
+      }
+    }
+    if (!fp64_project_dots<T, RPC>(D, sh, ctl, p, yv, 74)) return;
+    for (int c = threadIdx.x; c < p; c += TPB) sh.qv[c] = sh.sc[c];
+    __syncthreads();
+    fp64_comb_add<T, RPC>(D, p, sh.qv, -1.0, yv);
+#pragma unroll
+    for (int i = 0; i < RPC; i++) {
+      const int64_t ch = tid + i * TT;
+      if (ch < D.nchunks) stv(D.y64 + ch * W, yv[i]);
+    }
+    if (!grid_sync(D.st, sh, ctl, 75)) return;
+  }
+  // xi = -y - sum_{i != j} v_i c_i / (lambda_i - lambda_j)
+  if (threadIdx.x == 0)
+    for (int c = 0; c < p; c++) sh.qv[c] = (c == j) ? 0.0 : sh.cadj[c] / (D.st->lambda[c] - lam);
+  __syncthreads();
+  {
+    double xi[RPC][W];
+#pragma unroll
+    for (int i = 0; i < RPC; i++) {
+      const int64_t ch = tid + i * TT;
+      if (ch < D.nchunks) {
+        ldc(D.y64 + ch * W, xi[i]);
+#pragma unroll
+        for (int u = 0; u < W; u++) xi[i][u] = -xi[i][u];
+      } else {
+#pragma unroll
+        for (int u = 0; u < W; u++) xi[i][u] = 0.0;
+      }
+    }
+    fp64_comb_add<T, RPC>(D, p, sh.qv, -1.0, xi);
+#pragma unroll
+    for (int i = 0; i < RPC; i++) {
+      const int64_t ch = tid + i * TT;
+      if (ch < D.nchunks) stv(D.t + ch * W, xi[i]);
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    D.st->adj_refine = refine;
+    D.st->adj_inner = inner;
+    D.st->adj_res = res;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // host-side launch table.  This file is compiled once per (precision, RPC)
 // pair (NLE_T, NLE_RPC, NLE_TAG defined by the build) so that the
 // instantiations compile in parallel.
@@ -1102,6 +1313,7 @@ void *NLE_CAT(kernel_ptr_, NLE_TAG)(int id) {
     case 2: return (void *)k_shifted<NLE_T, NLE_RPC>;
     case 3: return (void *)k_prec<NLE_T, NLE_RPC>;
     case 4: return (void *)k_pcg<NLE_T, NLE_RPC>;
+    case 5: return (void *)k_adjoint<NLE_T, NLE_RPC>;
   }
   return nullptr;
 }

@@ -254,6 +254,18 @@ class Eigensolver:
         self._check(st, allow=(5,) if allow_noconv else ())
         return lam, V, stats_dict(stats)
 
+    def backward(self, gbar_lambda=None, gbar_V=None, grad=None):
+        """Accumulate dL/dA_e for every stored entry e into grad (created as
+        zeros when None) for the last solve; gbar_V is (p, n)."""
+        torch = self.torch
+        if grad is None:
+            grad = torch.zeros(self.nnz, dtype=torch.float64, device=self.dev)
+        gl = None if gbar_lambda is None else torch.as_tensor(gbar_lambda, dtype=torch.float64).to(self.dev).contiguous()
+        gv = None if gbar_V is None else torch.as_tensor(gbar_V, dtype=torch.float64).to(self.dev).contiguous()
+        self._check(nle_backward(self.h, _dptr(gl) if gl is not None else None, _dptr(gv) if gv is not None else None,
+                                 _dptr(grad), 1))
+        return grad
+
     def apply_shifted(self, theta: float, x):
         torch = self.torch
         x = torch.as_tensor(x, dtype=torch.float64).to(self.dev).contiguous()
@@ -299,3 +311,46 @@ def stats_dict(s: nle_stats) -> dict:
                 pcg_sum_k=int(s.pcg_sum_k), dacg_iterations=int(s.dacg_iterations), dacg_sum_m=int(s.dacg_sum_m),
                 kernel_launches=int(s.kernel_launches),
                 ms_phase=dict(zip(PHASES, [float(x) for x in s.ms_phase])), ascending=bool(s.ascending))
+
+
+def _eigsh_function():
+    import torch
+
+    class EigshFunction(torch.autograd.Function):
+        """(lambda, V) = leftmost p eigenpairs of the SPD matrix with a fixed CSR
+        pattern and values `values` (nnz, float64).  The backward pass is the
+        library's adjoint (nle_backward): dlambda_j/dA_ab = v_ja v_jb and the
+        eigenvector part through the projected PCG solve with shift lambda_j.
+        Entries (a,b) and (b,a) are independent inputs; a symmetric
+        parametrisation sums their gradients."""
+
+        @staticmethod
+        def forward(ctx, values, rowptr, col, p, tol, lfil, tau_ic, options, X0):
+            class _A:
+                pass
+
+            A = _A()
+            A.n = len(rowptr) - 1
+            A.rowptr = np.asarray(rowptr, dtype=np.int64)
+            A.col = np.asarray(col, dtype=np.int32)
+            A.val = values.detach().to("cpu", torch.float64).numpy()
+            s = Eigensolver(A, options)
+            s.factor_ic(lfil, tau_ic)
+            lam, V, stats = s.solve(p, tol, 100, 20, X0)
+            ctx.solver = s
+            return lam, V
+
+        @staticmethod
+        def backward(ctx, glam, gV):
+            s = ctx.solver
+            grad = s.backward(glam, gV)
+            s.close()
+            return grad.to(glam.device if glam is not None else grad.device), None, None, None, None, None, None, None, None
+
+    return EigshFunction
+
+
+def eigsh(values, rowptr, col, p: int, tol: float = 1e-8, lfil: int = 30, tau_ic: float = 1e-2, options=None,
+          X0=None):
+    """Differentiable leftmost eigenpairs (see EigshFunction)."""
+    return _eigsh_function().apply(values, rowptr, col, p, tol, lfil, tau_ic, options, X0)
