@@ -196,13 +196,19 @@ nle_status nle_solve(nle_t h, int p, double tol, int max_newton, int max_pcg, co
 nle_status nle_backward(nle_t h, const double *gbar_lambda, const double *gbar_V, double *grad_val,
                         int buffers_on_device);
 
-/* Solve `count` independent problems with one persistent launch per phase
- * (each CTA group works on one problem at a time; problems are taken from a
- * device work queue, largest first).  Every handle must have been factored;
- * all share p, tol, max_newton, max_pcg and use the options of hs[0].
+/* Solve `count` independent problems (each handle factored) in ONE
+ * persistent launch: groups of 4 CTAs take problems from a device work
+ * queue, largest n first, and each group runs the whole of Algorithm 3.2
+ * (DACG and Newton for every eigenpair) for its problem, then takes the next.
+ * Requirements: every handle was factored for at most 4 CTAs (create it with
+ * nle_options.grid_ctas = 4, or small enough n), all handles share the
+ * precision and the device; the options of hs[0] apply and the work runs on
+ * hs[0]'s stream.  p, tol, max_newton, max_pcg as in nle_solve.
  * lambdas[b] [p] and Vs[b] [p*n_b] are device pointers; X0s may be NULL or
- * an array of device pointers (entries may be NULL).  per_problem[b]
- * receives each problem's status; the return value is the worst of them. */
+ * an array of device pointers (entries may be NULL: fixed pseudo-random
+ * starts).  per_problem[b] (nullable) receives each problem's status; the
+ * return value is the worst of them.  Each handle then holds its solution
+ * for nle_backward. */
 nle_status nle_batch_solve(int count, nle_t *hs, int p, double tol, int max_newton, int max_pcg,
                            const double *const *X0s, double *const *lambdas, double *const *Vs,
                            nle_status *per_problem);

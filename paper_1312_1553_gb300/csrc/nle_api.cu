@@ -26,7 +26,7 @@ void *kernel_ptr_d1(int);
 void *kernel_ptr_d2(int);
 void *kernel_ptr_d4(int);
 void *kernel_ptr_d8(int);
-enum KernelId { K_NEWTON = 0, K_DACG = 1, K_SHIFTED = 2, K_PREC = 3, K_PCG = 4, K_ADJOINT = 5 };
+enum KernelId { K_NEWTON = 0, K_DACG = 1, K_SHIFTED = 2, K_PREC = 3, K_PCG = 4, K_ADJOINT = 5, K_BATCH = 6 };
 template <typename T>
 void *kernel_ptr(int id, int rpc);
 template <>
@@ -190,12 +190,14 @@ struct nle_ctx {
   DBuf part, state;
   DBuf scratch;  // 2 * n doubles for host transfers
   DBuf d_erow, d_ecol, d_grad;  // natural-order entries (adjoint)
+  DBuf dX0;                      // start vectors for the batched kernel (p columns, level order)
   std::vector<double> pinned_dummy;
   bool solved = false;
   int last_p = 0;
   std::vector<double> lambda;
   std::string err;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  float last_batch_ms = 0.f;  // device time of the last nle_batch_solve led by this handle
 };
 
 static thread_local std::string g_create_error;
@@ -251,6 +253,7 @@ static Dev<T> make_dev(nle_t h) {
   D.nchunks = h->nchunks;
   D.ldq = h->ldq;
   D.bsize = h->bsize;
+  D.grid = h->grid;
   const int64_t ns = h->npad / (32 * h->vw);
   D.A = {ns, h->A_sptr.as<int64_t>(), h->A_col.as<int32_t>(), h->A_val.as<T>()};
   D.A64 = {ns, h->A_sptr.as<int64_t>(), h->A_col.as<int32_t>(), h->A64_val.as<double>()};
@@ -853,15 +856,121 @@ extern "C" nle_status nle_backward(nle_t h, const double *gbar_lambda, const dou
                   : backward_impl<double>(h, gbar_lambda, gbar_V, grad_val, buffers_on_device);
 }
 
+template <typename T>
+static nle_status batch_impl(int count, nle_t *hs, int p, double tol, int max_newton, int max_pcg,
+                             const double *const *X0s, double *const *lambdas, double *const *Vs,
+                             nle_status *per_problem) {
+  nle_t h0 = hs[0];
+  constexpr int G = 4;  // CTAs per group
+  int rpc = 1;
+  size_t dyn = 0;
+  std::vector<Dev<T>> devs(count);
+  std::vector<int> order(count);
+  for (int b = 0; b < count; b++) {
+    nle_t h = hs[b];
+    nle_status s = ensure_q(h, p);
+    if (s != NLE_OK) return s;
+    const size_t tsz = sizeof(T);
+    if (h->dX0.bytes < (size_t)p * h->npad * tsz) NLE_CUDA(h0, dalloc(h->dX0, (size_t)p * h->npad * tsz));
+    Dev<T> D = make_dev<T>(h);
+    T *x0 = h->dX0.as<T>();
+    for (int j = 0; j < p; j++) {
+      if (X0s && X0s[b]) {
+        s = put_vectors<T>(h, X0s[b] + (int64_t)j * h->n, 1, x0 + (int64_t)j * h->npad, 1);
+      } else {
+        k_default_start<<<1024, 256, 0, h->stream>>>(h->scratch.as<double>(), h->n, j);
+        s = put_vectors<T>(h, h->scratch.as<double>(), 1, x0 + (int64_t)j * h->npad, 1);
+      }
+      if (s != NLE_OK) return s;
+    }
+    D.X0 = x0;
+    devs[b] = D;
+    NLE_CUDA(h0, cudaMemsetAsync(h->state.p, 0, sizeof(State), h->stream));
+    NLE_CUDA(h0, cudaStreamSynchronize(h->stream));
+    while ((int64_t)rpc * h->grid * TPB < h->nchunks) rpc *= 2;
+    dyn = std::max(dyn, (size_t)h->bsize * sizeof(T));
+    order[b] = b;
+  }
+  if (rpc > 8) return fail(h0, NLE_ERR_ARG, "a problem is too large for its CTA group");
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return hs[a]->n > hs[b]->n; });
+  const int ngroups = std::max(1, h0->nsm / G);
+  DBuf d_devs, d_order, d_ctl;
+  NLE_CUDA(h0, upload(d_devs, devs));
+  NLE_CUDA(h0, upload(d_order, order));
+  NLE_CUDA(h0, dalloc(d_ctl, (size_t)(1 + 3 * ngroups) * sizeof(int)));
+  Batch<T> B;
+  B.devs = d_devs.as<Dev<T>>();
+  B.order = d_order.as<int>();
+  B.count = count;
+  B.G = G;
+  B.p = p;
+  B.queue = d_ctl.as<unsigned>();
+  B.gbar = d_ctl.as<unsigned>() + 1;
+  B.gslot = d_ctl.as<int>() + 1 + ngroups;
+  B.gerr = d_ctl.as<int>() + 1 + 2 * ngroups;
+  B.group_spin_ns = (long long)(60.0 * 1e9);
+  Opts O = make_opts(h0, tol, max_newton, max_pcg);
+  void *fn = kernel_ptr<T>(K_BATCH, rpc);
+  if (!fn) return fail(h0, NLE_ERR_ARG, "no kernel instance for this size");
+  NLE_CUDA(h0, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+  int nb = 0;
+  NLE_CUDA(h0, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, TPB, dyn));
+  if (nb < 1) return fail(h0, NLE_ERR_CUDA, "batched kernel does not fit on an SM");
+  void *args[] = {&B, &O};
+  NLE_CUDA(h0, cudaEventRecord(h0->ev[0], h0->stream));
+  NLE_CUDA(h0, cudaLaunchCooperativeKernel(fn, dim3(ngroups * G), dim3(TPB), args, dyn, h0->stream));
+  NLE_CUDA(h0, cudaEventRecord(h0->ev[1], h0->stream));
+  NLE_CUDA(h0, cudaStreamSynchronize(h0->stream));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, h0->ev[0], h0->ev[1]);
+  h0->last_batch_ms = ms;
+  std::vector<int> gerr(ngroups);
+  NLE_CUDA(h0, cudaMemcpy(gerr.data(), B.gerr, ngroups * sizeof(int), cudaMemcpyDeviceToHost));
+  int group_err = 0;
+  for (int e : gerr) group_err = group_err ? group_err : e;
+  nle_status worst = NLE_OK;
+  for (int b = 0; b < count; b++) {
+    nle_t h = hs[b];
+    State st;
+    NLE_CUDA(h0, cudaMemcpy(&st, h->state.p, sizeof(State), cudaMemcpyDeviceToHost));
+    nle_status s = NLE_OK;
+    if (st.err != 0 || group_err != 0) {
+      s = (nle_status)(st.err ? st.err : group_err);
+    } else {
+      k_output_vectors<<<p, 1024, 0, h0->stream>>>(Vs[b], devs[b].Qt, h->d_iperm.as<int32_t>(), h->n, h->npad,
+                                                  devs[b].st);
+      NLE_CUDA(h0, cudaGetLastError());
+      NLE_CUDA(h0, cudaMemcpyAsync(lambdas[b], &h->state.as<State>()->lambda[0], p * sizeof(double),
+                                   cudaMemcpyDeviceToDevice, h0->stream));
+      for (int j = 0; j < p; j++)
+        if (!st.conv[j]) s = NLE_ERR_NOCONV;
+      h->lambda.assign(st.lambda, st.lambda + p);
+      h->last_p = p;
+      h->solved = true;
+    }
+    if (per_problem) per_problem[b] = s;
+    if (s != NLE_OK && (worst == NLE_OK || worst == NLE_ERR_NOCONV)) worst = s;
+  }
+  NLE_CUDA(h0, cudaStreamSynchronize(h0->stream));
+  return worst;
+}
+
 extern "C" nle_status nle_batch_solve(int count, nle_t *hs, int p, double tol, int max_newton, int max_pcg,
                                       const double *const *X0s, double *const *lambdas, double *const *Vs,
                                       nle_status *per_problem) {
   if (count < 1 || !hs || !lambdas || !Vs) return fail(nullptr, NLE_ERR_ARG, "bad nle_batch_solve arguments");
-  nle_status worst = NLE_OK;
   for (int b = 0; b < count; b++) {
-    nle_status s = nle_solve(hs[b], p, tol, max_newton, max_pcg, X0s ? X0s[b] : nullptr, lambdas[b], Vs[b], nullptr, 1);
-    if (per_problem) per_problem[b] = s;
-    if (s != NLE_OK && (worst == NLE_OK || s != NLE_ERR_NOCONV)) worst = s;
+    if (!hs[b]) return fail(nullptr, NLE_ERR_ARG, "NULL handle in the batch");
+    if (!hs[b]->factored) return fail(hs[b], NLE_ERR_STATE, "nle_factor_ic has not been called");
+    if (hs[b]->opt.precision != hs[0]->opt.precision || hs[b]->device != hs[0]->device)
+      return fail(hs[b], NLE_ERR_ARG, "all handles of a batch need the same precision and device");
+    if (hs[b]->grid > 4)
+      return fail(hs[b], NLE_ERR_ARG, "batched handles must be factored for at most 4 CTAs (nle_options.grid_ctas <= 4)");
+    if (p < 1 || p >= hs[b]->n || p > NLE_MAX_P || !lambdas[b] || !Vs[b])
+      return fail(hs[b], NLE_ERR_ARG, "bad p or output pointer");
   }
-  return worst;
+  if (!(tol > 0) || max_newton < 0 || max_pcg < 1) return fail(hs[0], NLE_ERR_ARG, "bad tolerance or iteration caps");
+  cudaSetDevice(hs[0]->device);
+  return mixed(hs[0]) ? batch_impl<float>(count, hs, p, tol, max_newton, max_pcg, X0s, lambdas, Vs, per_problem)
+                      : batch_impl<double>(count, hs, p, tol, max_newton, max_pcg, X0s, lambdas, Vs, per_problem);
 }

@@ -132,6 +132,17 @@ __device__ __forceinline__ void record_error(State *st, int code, int where) {
 }
 
 // ---------------------------------------------------------------------------
+// CTA group working on one problem: blocks [s_gbase, s_gbase + s_gsize).
+// A single-problem launch uses the whole grid; the batched kernel runs
+// several problems at once, one group of CTAs each.  Thread ownership,
+// barriers, reductions and triangular-solve slabs are group-relative.
+// ---------------------------------------------------------------------------
+__shared__ int s_gbase;
+__shared__ int s_gsize;
+__device__ __forceinline__ int grank() { return (int)blockIdx.x - s_gbase; }
+__device__ __forceinline__ bool lead_cta() { return (int)blockIdx.x == s_gbase; }
+
+// ---------------------------------------------------------------------------
 // per-CTA shared state
 // ---------------------------------------------------------------------------
 struct Shared {
@@ -163,7 +174,7 @@ struct Ctl {
 // `phase` (called right after a barrier, so the time covers the whole grid).
 enum { PH_SPMV = 0, PH_UPDATE = 1, PH_FWD = 2, PH_BWD = 3, PH_DOTS = 4, PH_DIR = 5, PH_OUTER = 6, PH_OTHER = 7 };
 __device__ __forceinline__ void tmark(Shared &sh, int phase) {
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  if (lead_cta() && threadIdx.x == 0) {
     const long long t = gtimer();
     sh.tacc[phase] += t - sh.tlast;
     sh.tlast = t;
@@ -179,7 +190,7 @@ __device__ __forceinline__ bool grid_sync(State *st, Shared &sh, Ctl &ctl, int w
   __syncthreads();
   if (threadIdx.x == 0) {
     ctl.epoch++;
-    const unsigned target = ctl.epoch * gridDim.x;
+    const unsigned target = ctl.epoch * (unsigned)s_gsize;
     __threadfence();
     red_release_add(&st->bar, 1u);
     long long t0 = 0;
@@ -222,22 +233,22 @@ __device__ __forceinline__ void red_put(Shared &sh, int slot, double v) {
 template <typename T>
 __device__ __forceinline__ void red_flush(const Dev<T> &D, Shared &sh, Ctl &ctl, int nslots) {
   __syncthreads();
-  double *part = D.part + (size_t)ctl.rbuf * RED_MAX * gridDim.x;
+  double *part = D.part + (size_t)ctl.rbuf * RED_MAX * s_gsize;
   for (int s = threadIdx.x; s < nslots; s += TPB) {
     double v = 0.0;
 #pragma unroll
     for (int w = 0; w < NWARP; w++) v += sh.red[w][s];
-    part[(size_t)s * gridDim.x + blockIdx.x] = v;
+    part[(size_t)s * s_gsize + grank()] = v;
   }
 }
 
 template <typename T>
 __device__ __forceinline__ void red_collect(const Dev<T> &D, Shared &sh, Ctl &ctl, int nslots) {
-  const double *part = D.part + (size_t)ctl.rbuf * RED_MAX * gridDim.x;
+  const double *part = D.part + (size_t)ctl.rbuf * RED_MAX * s_gsize;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int s = warp; s < nslots; s += NWARP) {
     double v = 0.0;
-    for (int b = lane; b < (int)gridDim.x; b += 32) v += __ldcg(part + (size_t)s * gridDim.x + b);
+    for (int b = lane; b < s_gsize; b += 32) v += __ldcg(part + (size_t)s * s_gsize + b);
     v = warp_sum(v);
     if (lane == 0) sh.sc[s] = v;
   }
@@ -259,8 +270,8 @@ __device__ __forceinline__ bool reduce_all(const Dev<T> &D, Shared &sh, Ctl &ctl
 // chunk c holds rows c*W .. c*W+W-1.  Backward sweeps use the mirrored
 // numbering nchunks-1-(t + i TT).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ int64_t gtid() { return (int64_t)blockIdx.x * TPB + threadIdx.x; }
-__device__ __forceinline__ int64_t gthreads() { return (int64_t)gridDim.x * TPB; }
+__device__ __forceinline__ int64_t gtid() { return (int64_t)grank() * TPB + threadIdx.x; }
+__device__ __forceinline__ int64_t gthreads() { return (int64_t)s_gsize * TPB; }
 
 // y[v] = sum_e val * x[col] for the W rows of one chunk of a SELL matrix.
 template <int W, typename TV, typename TX, typename TA>
@@ -457,7 +468,7 @@ __device__ __forceinline__ T trsv_dep(const T *x, const volatile T *stage, int64
 template <bool LOWER, typename T, typename RHS>
 __device__ __forceinline__ void trsv_block(const TriEll<T> &M, T *x, int64_t npad, int64_t bsize, int twarps,
                                            long long spin_ns, int sleep_ns, State *st, T *stage_mem, RHS rhs_of) {
-  const int64_t b0 = (int64_t)blockIdx.x * bsize;
+  const int64_t b0 = (int64_t)grank() * bsize;
   const int64_t b1 = min(npad, b0 + bsize);
   const int64_t nb = b1 > b0 ? b1 - b0 : 0;
   volatile T *stage = stage_mem;
@@ -469,8 +480,8 @@ __device__ __forceinline__ void trsv_block(const TriEll<T> &M, T *x, int64_t npa
   int64_t it = warp;
   if (warp < twarps && it < ngrp) {
     const int q = lane >> 3, g = lane & 7;
-    const int64_t base = __ldg(M.off + blockIdx.x);
-    const int wd = __ldg(M.width + blockIdx.x);
+    const int64_t base = __ldg(M.off + grank());
+    const int wd = __ldg(M.width + grank());
     TriPre<T> cur, nxt;
     trsv_fetch<LOWER, T>(M, b0, base, wd, ngrp, it, q, g, rhs_of, cur);
     for (;;) {

@@ -110,6 +110,8 @@ struct Dev {
   const uint8_t *Lround = nullptr, *Uround = nullptr;
   // working-precision vectors (npad; z and c0 have npad + 32*VW entries)
   T *p, *y, *s, *g, *z, *c0, *rT, *x, *Ax, *Ap;
+  const T *X0 = nullptr;  // optional: start vectors (p columns, level order) for the whole-solve kernel
+  int grid = 0;           // CTAs this problem's layout was built for (slabs)
   T *Q;        // npad * ldq, column c at Q + c*npad (converged v_1.. and u)
   T *S, *R;    // npad * KMAX, BFGS pairs by physical slot
   // FP64 vectors
@@ -119,6 +121,21 @@ struct Dev {
   // reductions / control
   double *part;  // 2 * RED_MAX * gridDim
   State *st;
+};
+
+// Batched solve: problems taken from a device work queue by groups of G CTAs.
+template <typename T>
+struct Batch {
+  const Dev<T> *devs;  // per problem
+  const int *order;    // problems, largest first
+  int count;
+  int G;               // CTAs per group (every problem's layout uses <= G)
+  int p;               // eigenpairs per problem
+  unsigned *queue;     // next index into order
+  unsigned *gbar;      // per group: barrier counter
+  int *gslot;          // per group: index taken by the group
+  int *gerr;           // per group: error word of the group barrier
+  long long group_spin_ns;
 };
 
 }  // namespace nle

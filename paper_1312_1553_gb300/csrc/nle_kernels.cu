@@ -240,7 +240,7 @@ __device__ __forceinline__ void trsv_backward(const Dev<T> &D, const Ctl &ctl) {
 
 template <typename T>
 __device__ __forceinline__ void reset_queues(const Dev<T> &D) {
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  if (lead_cta() && threadIdx.x == 0) {
     D.st->qf = 0u;
     D.st->qb = 0u;
   }
@@ -568,7 +568,11 @@ __device__ bool fp64_residual(const Dev<T> &D, Shared &sh, Ctl &ctl, const doubl
 }
 
 template <typename T>
-__device__ void load_state(const Dev<T> &D, Shared &sh, Ctl &ctl, const Opts &O) {
+__device__ void load_state(const Dev<T> &D, Shared &sh, Ctl &ctl, const Opts &O, int gbase = 0, int gsize = -1) {
+  if (threadIdx.x == 0) {
+    s_gbase = gbase;
+    s_gsize = gsize > 0 ? gsize : (int)gridDim.x;
+  }
   ctl.epoch = 0;
   ctl.rbuf = 0;
   ctl.spin_ns = O.spin_ns;
@@ -585,7 +589,7 @@ __device__ void load_state(const Dev<T> &D, Shared &sh, Ctl &ctl, const Opts &O)
 
 // add this launch's phase times to the state (CTA 0)
 __device__ __forceinline__ void flush_timers(State *st, Shared &sh) {
-  if (blockIdx.x == 0 && threadIdx.x == 0)
+  if (lead_cta() && threadIdx.x == 0)
     for (int q = 0; q < 8; q++) st->tphase[q] += sh.tacc[q];
 }
 
@@ -593,13 +597,9 @@ __device__ __forceinline__ void flush_timers(State *st, Shared &sh) {
 // Kernel: Newton iteration for eigenpair j (Algorithm 3.2, inner loop)
 // ---------------------------------------------------------------------------
 template <typename T, int RPC>
-__global__ void __launch_bounds__(TPB, 1) k_newton(Dev<T> D, Opts O) {
+__device__ bool newton_body(const Dev<T> &D, const Opts &O, Shared &sh, Ctl &ctl, int j) {
   constexpr int W = VT<T>::W;
-  __shared__ Shared sh;
-  Ctl ctl;
-  load_state(D, sh, ctl, O);
   const int64_t tid = gtid(), TT = gthreads();
-  const int j = D.st->j;
   const int m = j + 1;
   double *u = D.Qt + (int64_t)j * D.npad;
   int k = 0;  // pairs reset for every eigenpair
@@ -610,18 +610,18 @@ __global__ void __launch_bounds__(TPB, 1) k_newton(Dev<T> D, Opts O) {
   int pcg_sum = 0;
   int exits[5] = {0, 0, 0, 0, 0};
 
-  if (!fp64_rayleigh<T, RPC>(D, sh, ctl, u)) return;
+  if (!fp64_rayleigh<T, RPC>(D, sh, ctl, u)) return false;
   mvp++;
   double theta = sh.sc[0] / sh.sc[1];
-  if (!fp64_residual<T, RPC>(D, sh, ctl, u, theta, j)) return;
+  if (!fp64_residual<T, RPC>(D, sh, ctl, u, theta, j)) return false;
   double rnorm = sqrt(sh.sc[0]);
   tmark(sh, PH_OUTER);
   int it = 0;
   while (rnorm > O.tol * theta && it < O.max_newton) {
-    if (!gram<T, RPC>(D, sh, ctl, m, k)) return;
+    if (!gram<T, RPC>(D, sh, ctl, m, k)) return false;
     tmark(sh, PH_OTHER);
     PcgOut po;
-    if (!pcg_solve<T, RPC>(D, O, sh, ctl, m, k, theta, O.max_pcg, po)) return;
+    if (!pcg_solve<T, RPC>(D, O, sh, ctl, m, k, theta, O.max_pcg, po)) return false;
     mvp += po.its;
     pcg_total += po.its;
     pcg_sum += po.its;
@@ -690,7 +690,7 @@ __global__ void __launch_bounds__(TPB, 1) k_newton(Dev<T> D, Opts O) {
         }
         red_put(sh, 1 + c, acc);
       }
-      if (!reduce_all(D, sh, ctl, 1 + j, 42)) return;
+      if (!reduce_all(D, sh, ctl, 1 + j, 42)) return false;
     }
     // N2: u = (t - Qt (Qt^T t)) / ||.||  (re-orthogonalisation against the
     // converged eigenvectors, then normalisation)
@@ -721,18 +721,18 @@ __global__ void __launch_bounds__(TPB, 1) k_newton(Dev<T> D, Opts O) {
           stv(u + ch * W, tv[i]);
         }
       }
-      if (!grid_sync(D.st, sh, ctl, 43)) return;
+      if (!grid_sync(D.st, sh, ctl, 43)) return false;
     }
-    if (!fp64_rayleigh<T, RPC>(D, sh, ctl, u)) return;
+    if (!fp64_rayleigh<T, RPC>(D, sh, ctl, u)) return false;
     mvp++;
     theta = sh.sc[0] / sh.sc[1];
-    if (!fp64_residual<T, RPC>(D, sh, ctl, u, theta, j)) return;
+    if (!fp64_residual<T, RPC>(D, sh, ctl, u, theta, j)) return false;
     rnorm = sqrt(sh.sc[0]);
     tmark(sh, PH_OUTER);
     it++;
   }
   flush_timers(D.st, sh);
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  if (lead_cta() && threadIdx.x == 0) {
     State *st = D.st;
     st->theta = theta;
     st->rnorm = rnorm;
@@ -747,6 +747,15 @@ __global__ void __launch_bounds__(TPB, 1) k_newton(Dev<T> D, Opts O) {
     st->pcg_sum_k += sum_k;
     for (int e = 0; e < 5; e++) st->exits[e] += exits[e];
   }
+  return true;
+}
+
+template <typename T, int RPC>
+__global__ void __launch_bounds__(TPB, 1) k_newton(Dev<T> D, Opts O) {
+  __shared__ Shared sh;
+  Ctl ctl;
+  load_state(D, sh, ctl, O);
+  newton_body<T, RPC>(D, O, sh, ctl, D.st->j);
 }
 
 // ---------------------------------------------------------------------------
@@ -755,13 +764,9 @@ __global__ void __launch_bounds__(TPB, 1) k_newton(Dev<T> D, Opts O) {
 // On entry x holds the start vector; on exit Qt[:, j] holds u_0 (FP64).
 // ---------------------------------------------------------------------------
 template <typename T, int RPC>
-__global__ void __launch_bounds__(TPB, 1) k_dacg(Dev<T> D, Opts O) {
+__device__ bool dacg_body(const Dev<T> &D, const Opts &O, Shared &sh, Ctl &ctl, int j) {
   constexpr int W = VT<T>::W;
-  __shared__ Shared sh;
-  Ctl ctl;
-  load_state(D, sh, ctl, O);
   const int64_t tid = gtid(), TT = gthreads();
-  const int j = D.st->j;
   const int mq = j;  // converged eigenvectors (shadow columns of Q)
   const T Tsent = sentinel<T>();
   long long mvp = 0;
@@ -770,7 +775,7 @@ __global__ void __launch_bounds__(TPB, 1) k_dacg(Dev<T> D, Opts O) {
   for (int i = 0; i < RPC; i++) {
     const int64_t ch = tid + i * TT;
     if (ch < D.nchunks)
-      ldc(D.x + ch * W, xv[i]);
+      ldc((D.X0 ? D.X0 + (int64_t)j * D.npad : D.x) + ch * W, xv[i]);
     else
 #pragma unroll
       for (int v = 0; v < W; v++) xv[i][v] = T(0);
@@ -778,13 +783,13 @@ __global__ void __launch_bounds__(TPB, 1) k_dacg(Dev<T> D, Opts O) {
   // x0 projected on the complement of Q~ twice (classical Gram-Schmidt)
   for (int rep = 0; rep < 2 && mq > 0; rep++) {
     dots_put<T, RPC>(sh, 0, D.Q, D.npad, mq, nullptr, D, xv, false);
-    if (!reduce_all(D, sh, ctl, mq, 50)) return;
+    if (!reduce_all(D, sh, ctl, mq, 50)) return false;
     for (int c = threadIdx.x; c < mq; c += TPB) sh.qv[c] = -sh.sc[c];
     __syncthreads();
     comb_add<T, RPC>(D.Q, D.npad, mq, sh.qv, nullptr, D, xv, 1.0);
   }
   red_put(sh, 0, self_dot<T, RPC>(xv, xv));
-  if (!reduce_all(D, sh, ctl, 1, 51)) return;
+  if (!reduce_all(D, sh, ctl, 1, 51)) return false;
   {
     const T inv = T(1.0 / sqrt(sh.sc[0]));
 #pragma unroll
@@ -795,7 +800,7 @@ __global__ void __launch_bounds__(TPB, 1) k_dacg(Dev<T> D, Opts O) {
       if (ch < D.nchunks) stv(D.x + ch * W, xv[i]);
     }
   }
-  if (!grid_sync(D.st, sh, ctl, 52)) return;
+  if (!grid_sync(D.st, sh, ctl, 52)) return false;
   // Ax
 #pragma unroll
   for (int i = 0; i < RPC; i++) {
@@ -807,7 +812,7 @@ __global__ void __launch_bounds__(TPB, 1) k_dacg(Dev<T> D, Opts O) {
     }
   }
   mvp++;
-  if (!grid_sync(D.st, sh, ctl, 53)) return;
+  if (!grid_sync(D.st, sh, ctl, 53)) return false;
 
   double nx = 1.0, gg_prev = 0.0;
   int its = 0;
@@ -835,7 +840,7 @@ __global__ void __launch_bounds__(TPB, 1) k_dacg(Dev<T> D, Opts O) {
       }
       red_put(sh, 0, self_dot<T, RPC>(xv, av));
       red_put(sh, 1, self_dot<T, RPC>(xv, xv));
-      if (!reduce_all(D, sh, ctl, 2, 54)) return;
+      if (!reduce_all(D, sh, ctl, 2, 54)) return false;
       nx = 1.0;  // x and Ax now hold the normalised iterate
     }
     const double q = sh.sc[0], f = sh.sc[1];
@@ -858,7 +863,7 @@ __global__ void __launch_bounds__(TPB, 1) k_dacg(Dev<T> D, Opts O) {
       }
       reset_queues(D);
       red_put(sh, 0, self_dot<T, RPC>(gv, gv));
-      if (!reduce_all(D, sh, ctl, 1, 55)) return;
+      if (!reduce_all(D, sh, ctl, 1, 55)) return false;
       tmark(sh, PH_UPDATE);
     }
     if (sqrt(sh.sc[0]) <= O.tau_dacg * q) break;
@@ -867,7 +872,7 @@ __global__ void __launch_bounds__(TPB, 1) k_dacg(Dev<T> D, Opts O) {
     {
       // Phat_0 g via the preconditioner tail with no pairs, writing into Ap as
       // scratch: Ap = c0 - Q z, then p = -Ap + beta p below.
-      if (!precond_tail<T, RPC>(D, sh, ctl, mq, 0, D.Ap, 0.0, false, &gg)) return;
+      if (!precond_tail<T, RPC>(D, sh, ctl, mq, 0, D.Ap, 0.0, false, &gg)) return false;
       const double beta = (it == 0) ? 0.0 : gg / gg_prev;
 #pragma unroll
       for (int i = 0; i < RPC; i++) {
@@ -886,7 +891,7 @@ __global__ void __launch_bounds__(TPB, 1) k_dacg(Dev<T> D, Opts O) {
           stv(D.p + ch * W, pp);
         }
       }
-      if (!grid_sync(D.st, sh, ctl, 56)) return;
+      if (!grid_sync(D.st, sh, ctl, 56)) return false;
       tmark(sh, PH_DIR);
     }
     // P6: Ap = A p; line-search scalars
@@ -914,7 +919,7 @@ __global__ void __launch_bounds__(TPB, 1) k_dacg(Dev<T> D, Opts O) {
       red_put(sh, 1, b);
       red_put(sh, 2, d);
       red_put(sh, 3, e);
-      if (!reduce_all(D, sh, ctl, 4, 57)) return;
+      if (!reduce_all(D, sh, ctl, 4, 57)) return false;
       tmark(sh, PH_SPMV);
     }
     double al;
@@ -957,7 +962,7 @@ __global__ void __launch_bounds__(TPB, 1) k_dacg(Dev<T> D, Opts O) {
         }
       }
       red_put(sh, 0, xx);
-      if (!reduce_all(D, sh, ctl, 1, 58)) return;
+      if (!reduce_all(D, sh, ctl, 1, 58)) return false;
       nx = sqrt(sh.sc[0]);
       tmark(sh, PH_UPDATE);
     }
@@ -973,7 +978,7 @@ __global__ void __launch_bounds__(TPB, 1) k_dacg(Dev<T> D, Opts O) {
         }
       }
       mvp++;
-      if (!grid_sync(D.st, sh, ctl, 59)) return;
+      if (!grid_sync(D.st, sh, ctl, 59)) return false;
     }
     gg_prev = gg;
   }
@@ -994,12 +999,21 @@ __global__ void __launch_bounds__(TPB, 1) k_dacg(Dev<T> D, Opts O) {
     }
   }
   flush_timers(D.st, sh);
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  if (lead_cta() && threadIdx.x == 0) {
     D.st->dacg_its[j] = its;
     D.st->mvp_dacg += mvp;
     D.st->dacg_total += its;
     D.st->dacg_sum_m += (long long)its * mq;
   }
+  return true;
+}
+
+template <typename T, int RPC>
+__global__ void __launch_bounds__(TPB, 1) k_dacg(Dev<T> D, Opts O) {
+  __shared__ Shared sh;
+  Ctl ctl;
+  load_state(D, sh, ctl, O);
+  dacg_body<T, RPC>(D, O, sh, ctl, D.st->j);
 }
 
 // ---------------------------------------------------------------------------
@@ -1010,6 +1024,11 @@ __global__ void __launch_bounds__(TPB, 1) k_dacg(Dev<T> D, Opts O) {
 template <typename T, int RPC>
 __global__ void __launch_bounds__(TPB, 1) k_shifted(Dev<T> D, double theta) {
   constexpr int W = VT<T>::W;
+  if (threadIdx.x == 0) {
+    s_gbase = 0;
+    s_gsize = (int)gridDim.x;
+  }
+  __syncthreads();
   const int64_t tid = gtid(), TT = gthreads();
 #pragma unroll
   for (int i = 0; i < RPC; i++) {
@@ -1078,7 +1097,7 @@ __global__ void __launch_bounds__(TPB, 1) k_pcg(Dev<T> D, Opts O, int m, int k, 
   if (!gram<T, RPC>(D, sh, ctl, m, k)) return;
   PcgOut po;
   if (!pcg_solve<T, RPC>(D, O, sh, ctl, m, k, theta, max_pcg, po)) return;
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  if (lead_cta() && threadIdx.x == 0) {
     D.st->last_its = po.its;
     D.st->last_exit = po.exit;
     D.st->last_g0 = po.g0;
@@ -1291,10 +1310,89 @@ __global__ void __launch_bounds__(TPB, 1) k_adjoint(Dev<T> D, Opts O, int j, int
       if (ch < D.nchunks) stv(D.t + ch * W, xi[i]);
     }
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  if (lead_cta() && threadIdx.x == 0) {
     D.st->adj_refine = refine;
     D.st->adj_inner = inner;
     D.st->adj_res = res;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Kernel: batched solve.  Groups of B.G consecutive CTAs take problems from a
+// device work queue (largest first); a group runs the whole of Algorithm 3.2
+// for its problem (DACG and Newton for every eigenpair) with group-relative
+// barriers and reductions, then takes the next problem.  A problem whose
+// layout was built for g < G CTAs runs on the first g CTAs of the group.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ bool group_sync(const Batch<T> &B, int group, unsigned &gepoch, Shared &sh) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    gepoch++;
+    const unsigned target = gepoch * (unsigned)B.G;
+    __threadfence();
+    red_release_add(&B.gbar[group], 1u);
+    long long t0 = 0;
+    int spins = 0;
+    int ok = 1;
+    while (ld_acquire(&B.gbar[group]) < target) {
+      if (++spins >= 64) {
+        spins = 0;
+        __nanosleep(256);
+        if (ld_relaxed_int(&B.gerr[group]) != 0) {
+          ok = 0;
+          break;
+        }
+        const long long now = gtimer();
+        if (t0 == 0)
+          t0 = now;
+        else if (now - t0 > B.group_spin_ns) {
+          atomicExch(&B.gerr[group], 8 /*NLE_ERR_TIMEOUT*/);
+          ok = 0;
+          break;
+        }
+      }
+    }
+    __threadfence();
+    sh.ok = ok && ld_relaxed_int(&B.gerr[group]) == 0;
+  }
+  __syncthreads();
+  return sh.ok != 0;
+}
+
+template <typename T, int RPC>
+__global__ void __launch_bounds__(TPB, 1) k_batch(Batch<T> B, Opts O) {
+  __shared__ Shared sh;
+  __shared__ __align__(16) unsigned char sD_raw[sizeof(Dev<T>)];  // problem descriptor
+  Dev<T> &sD = *reinterpret_cast<Dev<T> *>(sD_raw);
+  __shared__ int s_idx;
+  const int group = (int)blockIdx.x / B.G, rank = (int)blockIdx.x % B.G;
+  unsigned gepoch = 0;
+  for (;;) {
+    if (rank == 0 && threadIdx.x == 0) {
+      const unsigned idx = atomicAdd(B.queue, 1u);
+      atomicExch(&B.gslot[group], (int)idx);
+    }
+    if (!group_sync(B, group, gepoch, sh)) return;
+    if (threadIdx.x == 0) s_idx = ld_relaxed_int(&B.gslot[group]);
+    __syncthreads();
+    const int idx = s_idx;
+    if (idx >= B.count) return;
+    if (threadIdx.x == 0) sD = B.devs[B.order[idx]];
+    __syncthreads();
+    const int gi = sD.grid;
+    if (rank < gi) {
+      Ctl ctl;
+      load_state(sD, sh, ctl, O, group * B.G, gi);
+      for (int j = 0; j < B.p; j++) {
+        if (!dacg_body<T, RPC>(sD, O, sh, ctl, j)) break;
+        if (!grid_sync(sD.st, sh, ctl, 80)) break;
+        if (!newton_body<T, RPC>(sD, O, sh, ctl, j)) break;
+        if (!grid_sync(sD.st, sh, ctl, 81)) break;
+      }
+    }
+    // every CTA of the group is done with this problem before the slot moves on
+    if (!group_sync(B, group, gepoch, sh)) return;
   }
 }
 
@@ -1314,6 +1412,7 @@ void *NLE_CAT(kernel_ptr_, NLE_TAG)(int id) {
     case 3: return (void *)k_prec<NLE_T, NLE_RPC>;
     case 4: return (void *)k_pcg<NLE_T, NLE_RPC>;
     case 5: return (void *)k_adjoint<NLE_T, NLE_RPC>;
+    case 6: return (void *)k_batch<NLE_T, NLE_RPC>;
   }
   return nullptr;
 }

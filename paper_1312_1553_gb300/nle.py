@@ -301,6 +301,29 @@ class Eigensolver:
         return s, dict(its=info.its, exit=EXITS[info.exit], gnorm0=info.gnorm0, gnorm=info.gnorm, eigres=info.eigres)
 
 
+def batch_solve(solvers, p: int, tol: float, max_newton: int = 100, max_pcg: int = 20, X0s=None):
+    """nle_batch_solve over Eigensolver objects (created with grid_ctas <= 4).
+    Returns (lambdas, Vs, statuses): lists of CUDA tensors and status codes."""
+    import torch
+
+    count = len(solvers)
+    dev = solvers[0].dev
+    lams = [torch.empty(p, dtype=torch.float64, device=dev) for _ in solvers]
+    Vs = [torch.empty((p, s.n), dtype=torch.float64, device=dev) for s in solvers]
+    x0t = None
+    if X0s is not None:
+        x0t = [torch.as_tensor(x, dtype=torch.float64).to(dev).contiguous() for x in X0s]
+    H = (ctypes.c_void_p * count)(*[s.h.value for s in solvers])
+    L = (ctypes.c_void_p * count)(*[t.data_ptr() for t in lams])
+    V = (ctypes.c_void_p * count)(*[t.data_ptr() for t in Vs])
+    X = (ctypes.c_void_p * count)(*[t.data_ptr() for t in x0t]) if x0t is not None else None
+    per = (ctypes.c_int * count)()
+    st = nle_batch_solve(count, H, p, tol, max_newton, max_pcg, X, L, V, per)
+    if st not in (NLE_OK, 5):
+        raise NLEError(st, nle_last_error(solvers[0].h))
+    return lams, Vs, list(per)
+
+
 def stats_dict(s: nle_stats) -> dict:
     p = s.p
     return dict(p=p, dacg_its=list(s.dacg_its[:p]), outer_its=list(s.outer_its[:p]), pcg_its=list(s.pcg_its[:p]),

@@ -1,0 +1,62 @@
+"""nle_batch_solve: many grounded graph Laplacians of uneven size in one
+persistent launch, against the single-problem solve and the oracle."""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def nle():
+    from paper_1312_1553_gb300 import _build, nle
+
+    _build.build()
+    nle.load_library()
+    return nle
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_batch_matches_single_and_oracle(nle, prec):
+    sizes = [2400, 5200, 3100, 7000, 2000, 4300]
+    mats = [W.geometric_graph_laplacian(n, 900 + i) for i, n in enumerate(sizes)]
+    p = 4
+    opts = dict(precision=nle.NLE_MIXED if prec == "mixed" else nle.NLE_FP64, grid_ctas=4)
+    solvers = []
+    X0s = []
+    for i, A in enumerate(mats):
+        s = nle.Eigensolver(A, opts)
+        s.factor_ic(30, 1e-2)
+        solvers.append(s)
+        X0s.append(W.start_vectors(A.n, p, 700 + i))
+    lams, Vs, per = nle.batch_solve(solvers, p, 1e-8, 100, 20, X0s)
+    assert all(x == 0 for x in per), per
+    rtol = 1e-8 if prec == "mixed" else 1e-10
+    for i, A in enumerate(mats):
+        lam = lams[i].cpu().numpy()
+        V = Vs[i].cpu().numpy()
+        assert abs(lam[0] - 1e-3) <= 1e-3 * rtol * 10
+        lref, Vref, _ = O.dacg_newton(A, p, X0s[i], O.OracleOptions(tol=1e-8, lfil=30, tau_ic=1e-2))
+        np.testing.assert_allclose(lam, lref, rtol=rtol)
+        Asp = A.to_scipy()
+        for j in range(p):
+            assert np.linalg.norm(Asp @ V[j] - lam[j] * V[j]) <= 1.5e-8 * lam[j]
+        # the single-problem path gives the same eigenvalues
+        l1, _, _ = solvers[i].solve(p, 1e-8, 100, 20, X0s[i])
+        np.testing.assert_allclose(l1.cpu().numpy(), lam, rtol=rtol)
+    for s in solvers:
+        s.close()
+
+
+def test_batch_rejects_wide_layout(nle):
+    """A handle factored for more than 4 CTAs cannot join a batch (its slab
+    layout is tied to its CTA count)."""
+    B = W.geometric_graph_laplacian(40000, 6)  # 10,000 row groups: 20 CTAs wanted
+    s = nle.Eigensolver(B, dict(precision=nle.NLE_MIXED, grid_ctas=8))
+    s.factor_ic(30, 1e-2)
+    with pytest.raises(nle.NLEError) as e:
+        nle.batch_solve([s], 2, 1e-8)
+    assert e.value.code == 1
+    s.close()
