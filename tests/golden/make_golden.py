@@ -23,6 +23,30 @@ import oracle as O  # noqa: E402
 import workloads as W  # noqa: E402
 
 
+def kappa_gradient(A, lam, V, opt):
+    """Gradient of loss = sum lambda_j + sum_i w_i (v_1)_i^2 with respect to the
+    cell coefficients, by the oracle's adjoint and the chain rule through
+    the assembly (torch CPU autograd), sampled at 64 seeded cells."""
+    import torch
+
+    p = len(lam)
+    ic = O.ic_factor(A, opt.lfil, opt.tau_ic)
+    w = A.meta["w"]
+    gl = np.ones(p)
+    gV = np.zeros((A.n, p))
+    gV[:, 0] = 2 * w * V[:, 0]
+    gA = O.adjoint_grad(A, lam, V, gl, gV, ic)
+    kappa = torch.tensor(A.meta["kappa"], dtype=torch.float64, requires_grad=True)
+    vals = W.diffusion_2d_values_torch(kappa)
+    (gk,) = torch.autograd.grad(vals, kappa, grad_outputs=torch.tensor(gA))
+    gk = gk.numpy().ravel()
+    rng = W.rng_for(4242)
+    cells = np.sort(rng.choice(A.n, size=64, replace=False))
+    loss = float(lam.sum() + w @ (V[:, 0] ** 2))
+    return dict(loss=loss, grad_cells=[int(c) for c in cells], grad_kappa=[float(gk[c]) for c in cells],
+                grad_kappa_norm=float(np.linalg.norm(gk)))
+
+
 def main(names):
     for name in names:
         A, st = W.workload(name)
@@ -40,6 +64,8 @@ def main(names):
                    oracle_seconds=sec, oracle_stats={k: stats[k] for k in
                                                      ("dacg_its", "outer_its", "pcg_its", "converged", "final_res",
                                                       "ascending", "nnz_L", "sigma")})
+        if name.startswith("diff2d5"):
+            out.update(kappa_gradient(A, lam, V, opt))
         with open(os.path.join(HERE, f"{name}.json"), "w") as fh:
             json.dump(out, fh, indent=1)
         print(name, sec, lam)

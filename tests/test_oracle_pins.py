@@ -506,3 +506,13 @@ def test_adjoint_eigenvector_finite_differences():
         e2 = np.flatnonzero((rows == A.col[e]) & (A.col == rows[e]))[0]
         sym = 0.5 * (grad[e] + grad[e2])
         assert abs(fd - sym) <= 1e-6 * max(1.0, abs(fd))
+
+
+def test_torch_assembly_matches_numpy_assembly():
+    """The differentiable assembly reproduces the stored values bit for bit
+    (so gradients with respect to entries map onto cell coefficients)."""
+    import torch
+
+    A = W.diffusion_2d_lognormal(9, 7, seed=5)
+    vals = W.diffusion_2d_values_torch(torch.tensor(A.meta["kappa"], dtype=torch.float64))
+    np.testing.assert_array_equal(vals.numpy(), A.val)

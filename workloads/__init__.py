@@ -250,6 +250,31 @@ def diffusion_2d_from_kappa(kappa: np.ndarray, name: str = "") -> CSR:
                         meta=dict(shape=(ny, nx), kappa=kappa))
 
 
+def diffusion_2d_values_torch(kappa):
+    """The stored values of diffusion_2d_from_kappa(kappa), in its CSR order,
+    as a differentiable function of the torch tensor kappa (ny, nx).
+
+    Used to carry gradients with respect to the matrix entries over to the
+    cell coefficients (chain rule through the harmonic-mean faces)."""
+    import torch
+
+    ny, nx = kappa.shape
+    fx = 2 * kappa[:, :-1] * kappa[:, 1:] / (kappa[:, :-1] + kappa[:, 1:])
+    fy = 2 * kappa[:-1, :] * kappa[1:, :] / (kappa[:-1, :] + kappa[1:, :])
+    west = torch.cat([kappa[:, :1], fx], dim=1)
+    east = torch.cat([fx, kappa[:, -1:]], dim=1)
+    south = torch.cat([kappa[:1, :], fy], dim=0)
+    north = torch.cat([fy, kappa[-1:, :]], dim=0)
+    diag = west + east + south + north
+    # entries per row in the assembler's order: south, west, diagonal, east, north
+    jj, ii = torch.meshgrid(torch.arange(ny), torch.arange(nx), indexing="ij")
+    cols = [(-south, jj > 0), (-west, ii > 0), (diag, torch.ones_like(ii, dtype=torch.bool)),
+            (-east, ii < nx - 1), (-north, jj < ny - 1)]
+    V = torch.stack([c.reshape(-1) for c, _ in cols], dim=1)
+    M = torch.stack([m.reshape(-1) for _, m in cols], dim=1)
+    return V[M]
+
+
 def diffusion_2d_lognormal(nx: int = 600, ny: int = 700, sigma: float = 0.5,
                            seed: int = BASE_SEED + 3) -> CSR:
     rng = rng_for(seed)
