@@ -281,6 +281,40 @@ def test_solve_full_size_100cubed(nle, prec):
     s.close()
 
 
+def test_solve_full_size_hex27_96(nle):
+    """n = 884,736 (27-point trilinear hex stiffness), p = 20, IC(20, 1e-4),
+    mixed precision: eigenvalues against the stored oracle run; eigenvector
+    samples within 10 tol lambda_j / gap_j (the eigenvector error allowed by
+    the residual test ||A v - lambda v|| <= tol lambda, on either side);
+    residuals, orthogonality, order; and the eigenvalue backward against the
+    identity sum_e A_e d(sum lambda)/dA_e = sum lambda (Rayleigh quotients
+    are homogeneous of degree 1 in the entries)."""
+    import torch
+
+    with open(os.path.join(HERE, "golden", "hex27_96.json")) as fh:
+        gold = json.load(fh)
+    A, st = load("hex27_96")
+    p = gold["p"]
+    X0 = W.start_vectors(A.n, p, st["seed"])
+    s = solver(nle, A, "mixed")
+    s.factor_ic(st["lfil"], st["tau_ic"])
+    lam_t, V_t, stats = s.solve(p, st["tol"], 100, 20, X0)
+    grad = s.backward(torch.ones(p, dtype=torch.float64), None).cpu().numpy()
+    s.close()
+    lam = lam_t.cpu().numpy()
+    V = V_t.cpu().numpy()
+    glam = np.array(gold["lam"])
+    np.testing.assert_allclose(lam, glam, rtol=1e-8)
+    gaps = np.minimum(np.diff(glam, prepend=-np.inf), np.diff(glam, append=np.inf))
+    idx = np.array(gold["sample_index"])
+    for j in range(p):
+        ref = np.array(gold["sample_V"][j])
+        v = align(V[j, idx], ref)
+        assert np.abs(v - ref).max() <= 10 * st["tol"] * glam[j] / gaps[j], j
+    _check_solution(A, lam, V, st["tol"])
+    assert abs(float(A.val @ grad) - lam.sum()) <= 1e-9 * lam.sum()
+
+
 # ---------------------------------------------------------------------------
 # edge cases and failure reporting
 # ---------------------------------------------------------------------------
