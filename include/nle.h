@@ -97,8 +97,18 @@ typedef struct {
   double spin_timeout_s; /* bound on each device-side wait, seconds (default 2.0) */
   int grid_ctas;         /* persistent grid size; 0 = one CTA per SM (default 0) */
   int trsv_warps;        /* warps per CTA in the triangular solves, 1..16 (default 16) */
-  int spin_sleep_ns;     /* back-off between polls of an unfinished row, ns (default 0) */
+  int ordering;          /* NLE_ORDER_NATURAL (default) or a multicolour ordering, see
+                            nle_multicolor_order; applied before the IC factor */
 } nle_options;
+
+/* Symmetric orderings applied by nle_factor_ic before the IC factor.  The
+ * paper factors A as given; a multicolour ordering factors P A P^T instead
+ * (a different IC preconditioner of the same eigenproblem) with far fewer
+ * levels in its triangular solves.  Inputs and outputs of every call stay
+ * in the caller's numbering. */
+#define NLE_ORDER_NATURAL 0
+#define NLE_ORDER_MULTICOLOR1 1 /* greedy colouring of the graph of A */
+#define NLE_ORDER_MULTICOLOR2 2 /* greedy colouring of the graph of A^2 (distance 2) */
 
 /* Per-solve statistics, mirroring the columns of the paper's tables
  * (DACG its, outer its, MVP, CPU) plus device timings. */
@@ -236,9 +246,24 @@ nle_status nle_pcg(nle_t h, double theta, double tol, int max_pcg, const double 
 /* Copy the IC factor out (host arrays).  Pass NULL for any output to only
  * query sizes.  L is CSR lower triangular with the diagonal last in each
  * row (nnzL entries, Lrowptr n+1); levL/levU: level of every row of L and
- * of U = L^T; *nlevL, *nlevU: number of levels. */
+ * of U = L^T; *nlevL, *nlevU: number of levels.  With a multicolour
+ * ordering the factor is that of P A P^T, in its numbering (row k of the
+ * factor is row perm[k] of A, perm from nle_multicolor_order). */
 nle_status nle_get_factor(nle_t h, int64_t *nnzL, int64_t *Lrowptr, int32_t *Lcol, double *Lval, int32_t *levL,
                           int32_t *levU, int64_t *nlevL, int64_t *nlevU);
+
+/* Greedy multicolour ordering of a symmetric sparsity pattern (host only,
+ * no device, no handle).  Not in the paper: it serves the optional
+ * reordering of nle_options.ordering.  Rows are coloured in natural order,
+ * each with the smallest colour not used by an already coloured row of its
+ * neighbourhood: {j != i : A_ij != 0} for distance 1, and additionally the
+ * neighbours of those rows for distance 2.  perm[k] (n entries, caller
+ * owned) lists the rows by colour, ascending row inside a colour, so
+ * P A P^T has row k = row perm[k] of A; *ncolors receives the number of
+ * colours.  NLE_ERR_ARG for distance not 1 or 2 or NULL pointers,
+ * NLE_ERR_CSR for a malformed pattern. */
+nle_status nle_multicolor_order(int64_t n, const int64_t *rowptr, const int32_t *col, int distance, int32_t *perm,
+                                int32_t *ncolors);
 
 /* ---- Allocation-free preconditioner application --------------------------
  * The paper has no counterpart to this call; it exists for callers that

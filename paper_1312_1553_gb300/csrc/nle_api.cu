@@ -310,7 +310,6 @@ static Opts make_opts(nle_t h, double tol, int max_newton, int max_pcg) {
   O.recompute = h->opt.dacg_recompute;
   O.spin_ns = (long long)(h->opt.spin_timeout_s * 1e9);
   O.trsv_warps = h->opt.trsv_warps;
-  O.spin_sleep_ns = h->opt.spin_sleep_ns;
   return O;
 }
 
@@ -401,7 +400,7 @@ void nle_default_options(nle_options *o) {
   o->spin_timeout_s = 2.0;
   o->grid_ctas = 0;
   o->trsv_warps = 16;
-  o->spin_sleep_ns = 0;
+  o->ordering = NLE_ORDER_NATURAL;
 }
 
 const char *nle_last_error(nle_t h) { return h ? h->err.c_str() : g_create_error.c_str(); }
@@ -430,7 +429,8 @@ nle_status nle_create(int64_t n, int64_t nnz, const int64_t *rowptr, const int32
   if (h->opt.precision != NLE_FP64 && h->opt.precision != NLE_MIXED) return fail(nullptr, NLE_ERR_ARG, "bad precision");
   if (!(h->opt.spin_timeout_s > 0)) return fail(nullptr, NLE_ERR_ARG, "spin_timeout_s must be positive");
   if (h->opt.trsv_warps < 1 || h->opt.trsv_warps > NWARP) return fail(nullptr, NLE_ERR_ARG, "trsv_warps out of range");
-  if (h->opt.spin_sleep_ns < 0 || h->opt.spin_sleep_ns > 100000) return fail(nullptr, NLE_ERR_ARG, "spin_sleep_ns out of range");
+  if (h->opt.ordering < NLE_ORDER_NATURAL || h->opt.ordering > NLE_ORDER_MULTICOLOR2)
+    return fail(nullptr, NLE_ERR_ARG, "unknown ordering");
   h->n = n;
   h->nnz = nnz;
   h->rowptr.resize(n + 1);
@@ -463,6 +463,33 @@ nle_status nle_create(int64_t n, int64_t nnz, const int64_t *rowptr, const int32
   return NLE_OK;
 }
 
+nle_status nle_multicolor_order(int64_t n, const int64_t *rowptr, const int32_t *col, int distance, int32_t *perm,
+                                int32_t *ncolors) {
+  if (n < 1 || !rowptr || !col || !perm || !ncolors || (distance != 1 && distance != 2)) {
+    g_create_error = "nle_multicolor_order: need n >= 1, non-NULL arrays and distance 1 or 2";
+    return NLE_ERR_ARG;
+  }
+  if (rowptr[0] != 0) {
+    g_create_error = "nle_multicolor_order: rowptr[0] != 0";
+    return NLE_ERR_CSR;
+  }
+  for (int64_t i = 0; i < n; i++) {
+    if (rowptr[i + 1] < rowptr[i]) {
+      g_create_error = "nle_multicolor_order: rowptr decreases at row " + std::to_string(i);
+      return NLE_ERR_CSR;
+    }
+    for (int64_t e = rowptr[i]; e < rowptr[i + 1]; e++)
+      if (col[e] < 0 || col[e] >= n) {
+        g_create_error = "nle_multicolor_order: column out of range in row " + std::to_string(i);
+        return NLE_ERR_CSR;
+      }
+  }
+  std::vector<int32_t> P;
+  *ncolors = multicolor_order(n, rowptr, col, distance, P);
+  memcpy(perm, P.data(), n * sizeof(int32_t));
+  return NLE_OK;
+}
+
 nle_status nle_factor_ic(nle_t h, int lfil, double tau_ic) {
   if (!h) return fail(nullptr, NLE_ERR_ARG, "NULL handle");
   if (lfil < 0 || !(tau_ic >= 0.0)) return fail(h, NLE_ERR_ARG, "need lfil >= 0 and tau_ic >= 0");
@@ -470,8 +497,23 @@ nle_status nle_factor_ic(nle_t h, int lfil, double tau_ic) {
   h->factored = false;
   h->solved = false;
   int64_t bad = -1;
+  // the matrix factored: A itself, or P A P^T for a multicolour ordering
+  const int64_t *rp = h->rowptr.data();
+  const int32_t *ci = h->col.data();
+  const double *va = h->val.data();
+  std::vector<int32_t> P0;
+  std::vector<int64_t> brp;
+  std::vector<int32_t> bci;
+  std::vector<double> bva;
+  if (h->opt.ordering != NLE_ORDER_NATURAL) {
+    multicolor_order(h->n, rp, ci, h->opt.ordering, P0);
+    permute_csr(h->n, rp, ci, va, P0, brp, bci, bva);
+    rp = brp.data();
+    ci = bci.data();
+    va = bva.data();
+  }
   Factor F;
-  if (ic_factor_host(h->n, h->rowptr.data(), h->col.data(), h->val.data(), lfil, tau_ic, F, &bad) != 0)
+  if (ic_factor_host(h->n, rp, ci, va, lfil, tau_ic, F, &bad) != 0)
     return fail(h, NLE_ERR_NOT_SPD, "non-positive pivot in IC column " + std::to_string(bad));
   h->F = std::move(F);
   const int H = 32 * h->vw;
@@ -495,9 +537,17 @@ nle_status nle_factor_ic(nle_t h, int lfil, double tau_ic) {
   h->bsize = ((h->npad + 4 * grid - 1) / (4 * grid)) * 4;
   if (h->bsize * (int64_t)(mixed(h) ? 4 : 8) > 160 * 1024)
     return fail(h, NLE_ERR_ARG, "n too large for the shared-memory slab of one persistent grid");
-  slab_level_order(h->F, h->bsize, h->perm, h->iperm);
+  // with a multicolour ordering the slabs still follow the caller's row
+  // order (P0[k] = caller's row of row k of P A P^T), which keeps each
+  // slab's rows and their neighbours together
+  slab_level_order(h->F, h->bsize, P0.empty() ? nullptr : P0.data(), h->perm, h->iperm);
   Permuted P;
-  permute(h->n, h->rowptr.data(), h->col.data(), h->val.data(), h->F, h->perm, h->iperm, h->npad, P);
+  permute(h->n, rp, ci, va, h->F, h->perm, h->iperm, h->npad, P);
+  if (!P0.empty()) {
+    // device position -> row of the caller's numbering, through P A P^T
+    for (int64_t p = 0; p < h->n; p++) h->perm[p] = P0[h->perm[p]];
+    for (int64_t p = 0; p < h->n; p++) h->iperm[h->perm[p]] = (int32_t)p;
+  }
   const size_t tsz = mixed(h) ? 4 : 8;
   if (mixed(h)) {
     SellSet<float> S;

@@ -167,7 +167,6 @@ struct Ctl {
   int rbuf;        // reduction buffer parity
   long long spin_ns;
   int twarps;      // warps of this CTA that take part in the triangular solves
-  int sleep_ns;    // poll back-off
 };
 
 // Phase timers: CTA 0 / thread 0 charges the time since the last mark to
@@ -315,69 +314,6 @@ __device__ __forceinline__ void sell_rows(const Sell<TV> &M, const TX *__restric
   }
 }
 
-// Wait (bounded) for a solve output to leave the not-yet-computed state.
-// With sleep_ns > 0 the poll is pipelined: four loads of the awaited value
-// are kept in flight, issued sleep_ns apart, so a value is seen about one
-// L2 round trip after it lands instead of up to two.  The bound uses the
-// SM cycle counter (spin_ns * 2.1 cycles; longer in real time at lower
-// clocks, never shorter than spin_ns at the 2.07 GHz maximum).
-template <typename T>
-__device__ __noinline__ T spin_value(const T *p, T v, State *st, long long spin_ns, int sleep_ns) {
-  const long long c0 = clock64();
-  const long long lim = spin_ns * 21 / 10;
-  if (sleep_ns <= 0) {
-    while (is_sent(v)) {
-      v = ld_relaxed(p);
-      if (is_sent(v) && clock64() - c0 > lim) {
-        record_error(st, 8 /*NLE_ERR_TIMEOUT*/, 100);
-        return T(0);
-      }
-    }
-    return v;
-  }
-  T r0 = ld_relaxed(p);
-  __nanosleep(sleep_ns);
-  T r1 = ld_relaxed(p);
-  __nanosleep(sleep_ns);
-  T r2 = ld_relaxed(p);
-  __nanosleep(sleep_ns);
-  T r3 = ld_relaxed(p);
-  for (;;) {
-    if (!is_sent(r0)) return r0;
-    __nanosleep(sleep_ns);
-    r0 = ld_relaxed(p);
-    if (!is_sent(r1)) return r1;
-    __nanosleep(sleep_ns);
-    r1 = ld_relaxed(p);
-    if (!is_sent(r2)) return r2;
-    __nanosleep(sleep_ns);
-    r2 = ld_relaxed(p);
-    if (!is_sent(r3)) return r3;
-    __nanosleep(sleep_ns);
-    r3 = ld_relaxed(p);
-    if (clock64() - c0 > lim) {
-      record_error(st, 8 /*NLE_ERR_TIMEOUT*/, 100);
-      return T(0);
-    }
-  }
-}
-
-// Wait (bounded) for a value staged in this CTA's shared memory.
-template <typename T>
-__device__ __noinline__ T spin_shared(const volatile T *p, State *st, long long spin_ns) {
-  const long long c0 = clock64();
-  const long long lim = spin_ns * 21 / 10;
-  T v = *p;
-  while (is_sent(v)) {
-    v = *p;
-    if (is_sent(v) && clock64() - c0 > lim) {
-      record_error(st, 8 /*NLE_ERR_TIMEOUT*/, 101);
-      return T(0);
-    }
-  }
-  return v;
-}
-
 // Sync-free triangular solve, one slab of rows per CTA.
 //
 // The unknowns are labelled slab-major, level-minor: CTA c owns positions
@@ -385,22 +321,24 @@ __device__ __noinline__ T spin_shared(const volatile T *p, State *st, long long 
 // order sorted by the level of each row in L.  A dependency inside the slab
 // is read from the CTA's shared-memory copy of the slab's results; one in
 // another slab (lower slabs for L, higher for L^T) is polled in global memory
-// with relaxed loads.  On the naturally ordered grids the solver meets, most
-// dependency chains stay inside a slab, so most hops cost a shared-memory
-// round trip instead of an L2 one.  Results start as a NaN payload that GPU
-// arithmetic never produces and are published both to shared and to global
-// memory; the value is its own ready flag.
+// with relaxed loads.  Results start as a NaN payload that GPU arithmetic
+// never produces and are published both to shared and to global memory; the
+// value is its own ready flag.
 //
 // Each slab stores its rows in ELL form (width = the slab's longest row,
 // rounded up to 8), so the address of a row's entries follows from the row
 // index without a dependent load.  A warp takes four consecutive rows at a
 // time, 8 lanes per row, two entries per lane in flight, and fetches the
-// next group's entries, right-hand sides and diagonals before the current
-// group waits.  Rows of a group that depend on each other are done in
-// rounds (round[r] = longest chain to r inside its group, precomputed)
-// separated by __syncwarp, so a lane never waits for a lane of its own warp.
-// Every wait is bounded; since every warp and CTA is resident (cooperative
-// launch) and works in dependency order, every wait ends.
+// next group's entries, right-hand sides and pivots (as reciprocals, so no
+// division sits on the dependency chain) before the current group waits.
+// The wait is warp-uniform: the warp re-polls the entries still missing
+// until every lane holds its values (a vote), then reduces with shuffles; a
+// per-lane wait followed by the warp's reconvergence measured about 1.5x
+// slower per dependency hop.  Rows of a group that depend on each other are
+// done in rounds (round[r] = longest chain to r inside its group,
+// precomputed) separated by __syncwarp, so a lane never waits for a lane of
+// its own warp.  Every wait is bounded; since every warp and CTA is resident
+// (cooperative launch) and works in dependency order, every wait ends.
 template <typename T>
 struct TriEll {
   const int64_t *off;    // per slab: first entry
@@ -415,7 +353,7 @@ template <typename T>
 struct TriPre {
   int c0, c1;
   T a0, a1;
-  T rhs, dg;
+  T rhs, rdg;  // right-hand side and 1 / pivot (lane g == 0 of each row)
   int rnd;
 };
 
@@ -435,39 +373,51 @@ __device__ __forceinline__ void trsv_fetch(const TriEll<T> &M, int64_t b0, int64
   }
   P.rnd = __ldg(M.round + r);
   P.rhs = T(0);
-  P.dg = T(1);
+  P.rdg = T(1);
   if (g == 0) {
     P.rhs = rhs_of(r);
-    P.dg = __ldg(M.diag + r);
+    P.rdg = T(1) / __ldg(M.diag + r);
   }
 }
 
-// Value of dependency c: the shared copy inside the slab, global memory
-// outside.  The poll is inlined and checks no clock for its first 2^20
-// tries (a call per poll measurably slowed every dependency hop); after that
-// the bounded wait takes over.
+// Current value of dependency c: the shared copy inside the slab, global
+// memory outside it (the not-yet-computed marker if it is not ready).
 template <typename T>
-__device__ __forceinline__ T trsv_dep(const T *x, const volatile T *stage, int64_t b0, int64_t b1, int c, State *st,
-                                      long long spin_ns, int sleep_ns) {
-  if (c >= b0 && c < b1) {
-    T v = stage[c - b0];
-    for (int k = 0; is_sent(v); k++) {
-      if (k == (1 << 20)) return spin_shared(stage + (c - b0), st, spin_ns);
-      v = stage[c - b0];
+__device__ __forceinline__ T trsv_peek(const T *x, const volatile T *stage, int64_t b0, int64_t b1, int c) {
+  return (c >= b0 && c < b1) ? stage[c - b0] : ld_relaxed(x + c);
+}
+
+// Warp-uniform wait: returns once every lane of the warp holds values (not
+// the marker) for its entries c0 and c1 (c < 0: no entry).  The clock is
+// read only after 2^20 rounds of polling; past spin_ns the wait records
+// NLE_ERR_TIMEOUT and substitutes 0 so that dependants still finish.
+template <typename T>
+__device__ __forceinline__ void trsv_wait(const T *x, const volatile T *stage, int64_t b0, int64_t b1, int c0, int c1,
+                                          T &v0, T &v1, State *st, long long spin_ns) {
+  bool ok = !(c0 >= 0 && is_sent(v0)) && !(c1 >= 0 && is_sent(v1));
+  if (__all_sync(0xffffffffu, ok)) return;
+  long long t0 = 0;
+  for (int k = 0;; k++) {
+    if (c0 >= 0 && is_sent(v0)) v0 = trsv_peek(x, stage, b0, b1, c0);
+    if (c1 >= 0 && is_sent(v1)) v1 = trsv_peek(x, stage, b0, b1, c1);
+    ok = !(c0 >= 0 && is_sent(v0)) && !(c1 >= 0 && is_sent(v1));
+    if (__all_sync(0xffffffffu, ok)) return;
+    if (k >= (1 << 20)) {
+      if (k == (1 << 20)) t0 = clock64();
+      const bool late = clock64() - t0 > spin_ns * 21 / 10;  // cycles at about 2.1 GHz
+      if (__any_sync(0xffffffffu, late)) {
+        if (!ok) record_error(st, 8 /*NLE_ERR_TIMEOUT*/, 102);
+        if (c0 >= 0 && is_sent(v0)) v0 = T(0);
+        if (c1 >= 0 && is_sent(v1)) v1 = T(0);
+        return;
+      }
     }
-    return v;
   }
-  T v = ld_relaxed(x + c);
-  for (int k = 0; is_sent(v); k++) {
-    if (k == (1 << 20)) return spin_value(x + c, v, st, spin_ns, sleep_ns);
-    v = ld_relaxed(x + c);
-  }
-  return v;
 }
 
 template <bool LOWER, typename T, typename RHS>
 __device__ __forceinline__ void trsv_block(const TriEll<T> &M, T *x, int64_t npad, int64_t bsize, int twarps,
-                                           long long spin_ns, int sleep_ns, State *st, T *stage_mem, RHS rhs_of) {
+                                           long long spin_ns, State *st, T *stage_mem, RHS rhs_of) {
   const int64_t b0 = (int64_t)grank() * bsize;
   const int64_t b1 = min(npad, b0 + bsize);
   const int64_t nb = b1 > b0 ? b1 - b0 : 0;
@@ -494,20 +444,28 @@ __device__ __forceinline__ void trsv_block(const TriEll<T> &M, T *x, int64_t npa
       const int rounds = 1 + __reduce_max_sync(0xffffffffu, (unsigned)cur.rnd);
       for (int rd = 0; rd < rounds; rd++) {
         const bool active = (cur.rnd == rd);
+        const int c0 = active ? cur.c0 : -1, c1 = active ? cur.c1 : -1;
+        T v0 = T(0), v1 = T(0);
+        if (c0 >= 0) v0 = trsv_peek(x, stage, b0, b1, c0);
+        if (c1 >= 0) v1 = trsv_peek(x, stage, b0, b1, c1);
+        trsv_wait(x, stage, b0, b1, c0, c1, v0, v1, st, spin_ns);
         T acc = T(0);
-        if (active) {
-          if (cur.c0 >= 0) acc = cur.a0 * trsv_dep(x, stage, b0, b1, cur.c0, st, spin_ns, sleep_ns);
-          if (cur.c1 >= 0) acc += cur.a1 * trsv_dep(x, stage, b0, b1, cur.c1, st, spin_ns, sleep_ns);
-          const int64_t e = base + (r - b0) * wd;
-          for (int k = g + 16; k < wd; k += 8) {
-            const int c = __ldg(M.col + e + k);
-            if (c >= 0) acc += __ldg(M.val + e + k) * trsv_dep(x, stage, b0, b1, c, st, spin_ns, sleep_ns);
-          }
+        if (c0 >= 0) acc = cur.a0 * v0;
+        if (c1 >= 0) acc += cur.a1 * v1;
+        // entries beyond the first two per lane (rows longer than 16); the
+        // trip count (wd - 16) / 8 is the same for every lane
+        const int64_t e = base + (r - b0) * wd;
+        for (int k = g + 16; k < wd; k += 8) {
+          const int c = active ? __ldg(M.col + e + k) : -1;
+          T v = T(0), none = T(0);
+          if (c >= 0) v = trsv_peek(x, stage, b0, b1, c);
+          trsv_wait(x, stage, b0, b1, c, -1, v, none, st, spin_ns);
+          if (c >= 0) acc += __ldg(M.val + e + k) * v;
         }
 #pragma unroll
         for (int o = 4; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
         if (active && g == 0) {
-          const T v = (cur.rhs - acc) / cur.dg;
+          const T v = (cur.rhs - acc) * cur.rdg;
           stage[r - b0] = v;
           st_relaxed(x + r, v);
         }

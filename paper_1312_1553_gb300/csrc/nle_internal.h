@@ -87,7 +87,6 @@ struct Opts {
   int recompute;
   long long spin_ns;
   int trsv_warps;     // warps per CTA that take part in the triangular solves
-  int spin_sleep_ns;  // back-off between polls of a not-yet-computed value
 };
 
 // Pointers handed to the persistent kernels (by value).

@@ -219,7 +219,7 @@ extern __shared__ __align__(16) unsigned char nle_dyn_smem[];  // slab of the tr
 template <typename T>
 __device__ __forceinline__ void trsv_forward(const Dev<T> &D, Shared &sh, const Ctl &ctl, int k) {
   const TriEll<T> L{D.Loff, D.Lw, D.Lcol, D.Lval, D.diag, D.Lround};
-  trsv_block<true, T>(L, D.z, D.npad, D.bsize, ctl.twarps, ctl.spin_ns, ctl.sleep_ns, D.st,
+  trsv_block<true, T>(L, D.z, D.npad, D.bsize, ctl.twarps, ctl.spin_ns, D.st,
                       reinterpret_cast<T *>(nle_dyn_smem), [&](int64_t r) {
                         T w = __ldcg(D.g + r);
                         for (int t = 0; t < k; t++)
@@ -234,7 +234,7 @@ __device__ __forceinline__ void trsv_forward(const Dev<T> &D, Shared &sh, const 
 template <typename T>
 __device__ __forceinline__ void trsv_backward(const Dev<T> &D, const Ctl &ctl) {
   const TriEll<T> U{D.Uoff, D.Uw, D.Ucol, D.Uval, D.diag, D.Uround};
-  trsv_block<false, T>(U, D.c0, D.npad, D.bsize, ctl.twarps, ctl.spin_ns, ctl.sleep_ns, D.st,
+  trsv_block<false, T>(U, D.c0, D.npad, D.bsize, ctl.twarps, ctl.spin_ns, D.st,
                        reinterpret_cast<T *>(nle_dyn_smem), [&](int64_t r) { return __ldcg(D.z + r); });
 }
 
@@ -577,7 +577,6 @@ __device__ void load_state(const Dev<T> &D, Shared &sh, Ctl &ctl, const Opts &O,
   ctl.rbuf = 0;
   ctl.spin_ns = O.spin_ns;
   ctl.twarps = max(1, min(NWARP, O.trsv_warps));
-  ctl.sleep_ns = O.spin_sleep_ns;
   if (threadIdx.x == 0) {
     sh.ok = 1;
     for (int s = 0; s < KMAX; s++) sh.order[s] = s;

@@ -226,17 +226,77 @@ int ic_factor_host(int64_t n, const int64_t *rp, const int32_t *ci, const double
   return 0;
 }
 
-void slab_level_order(const Factor &F, int64_t bsize, std::vector<int32_t> &perm, std::vector<int32_t> &iperm) {
+// Greedy colouring in natural order: row i takes the smallest colour not
+// held by an already coloured row of its neighbourhood ({j != i : A_ij != 0},
+// plus the neighbours of those rows for distance 2).  used[c] == i + 1
+// marks colour c as taken for row i, so the marks need no clearing.
+int32_t multicolor_order(int64_t n, const int64_t *rp, const int32_t *ci, int distance, std::vector<int32_t> &perm) {
+  std::vector<int32_t> color(n, -1);
+  std::vector<int64_t> used;
+  int32_t ncol = 0;
+  for (int64_t i = 0; i < n; i++) {
+    auto take = [&](int64_t j) {
+      if (j == i || color[j] < 0) return;
+      const int32_t c = color[j];
+      if ((size_t)c >= used.size()) used.resize((size_t)c + 1, 0);
+      used[c] = i + 1;
+    };
+    for (int64_t e = rp[i]; e < rp[i + 1]; e++) {
+      const int64_t j = ci[e];
+      take(j);
+      if (distance == 2)
+        for (int64_t f = rp[j]; f < rp[j + 1]; f++) take(ci[f]);
+    }
+    int32_t c = 0;
+    while ((size_t)c < used.size() && used[c] == i + 1) c++;
+    color[i] = c;
+    ncol = std::max(ncol, c + 1);
+  }
+  // counting sort by colour, stable in the row index
+  std::vector<int64_t> start((size_t)ncol + 1, 0);
+  for (int64_t i = 0; i < n; i++) start[color[i] + 1]++;
+  for (int32_t c = 0; c < ncol; c++) start[c + 1] += start[c];
+  perm.assign(n, 0);
+  for (int64_t i = 0; i < n; i++) perm[start[color[i]]++] = (int32_t)i;
+  return ncol;
+}
+
+void permute_csr(int64_t n, const int64_t *rp, const int32_t *ci, const double *va, const std::vector<int32_t> &perm,
+                 std::vector<int64_t> &brp, std::vector<int32_t> &bci, std::vector<double> &bva) {
+  std::vector<int32_t> iperm(n);
+  for (int64_t k = 0; k < n; k++) iperm[perm[k]] = (int32_t)k;
+  brp.assign(n + 1, 0);
+  for (int64_t k = 0; k < n; k++) brp[k + 1] = brp[k] + (rp[perm[k] + 1] - rp[perm[k]]);
+  bci.resize(brp[n]);
+  bva.resize(brp[n]);
+  std::vector<std::pair<int32_t, double>> row;
+  for (int64_t k = 0; k < n; k++) {
+    const int64_t i = perm[k];
+    row.clear();
+    for (int64_t e = rp[i]; e < rp[i + 1]; e++) row.emplace_back(iperm[ci[e]], va[e]);
+    std::sort(row.begin(), row.end(), [](const std::pair<int32_t, double> &a, const std::pair<int32_t, double> &b) {
+      return a.first < b.first;
+    });
+    for (size_t t = 0; t < row.size(); t++) {
+      bci[brp[k] + (int64_t)t] = row[t].first;
+      bva[brp[k] + (int64_t)t] = row[t].second;
+    }
+  }
+}
+
+void slab_level_order(const Factor &F, int64_t bsize, const int32_t *locality, std::vector<int32_t> &perm,
+                      std::vector<int32_t> &iperm) {
   const int64_t n = F.n;
   perm.resize(n);
   for (int64_t i = 0; i < n; i++) perm[i] = (int32_t)i;
-  // slabs are contiguous ranges of the natural order, so sorting by
-  // (slab, level, row) keeps every row inside its slab
+  auto loc = [&](int32_t r) -> int64_t { return locality ? locality[r] : r; };
+  // every slab holds bsize consecutive locality values, so sorting by
+  // (slab, level, locality) fills each slab's position range exactly
   std::sort(perm.begin(), perm.end(), [&](int32_t a, int32_t b) {
-    const int64_t sa = a / bsize, sb = b / bsize;
+    const int64_t sa = loc(a) / bsize, sb = loc(b) / bsize;
     if (sa != sb) return sa < sb;
     if (F.levL[a] != F.levL[b]) return F.levL[a] < F.levL[b];
-    return a < b;
+    return loc(a) < loc(b);
   });
   iperm.assign(n, 0);
   for (int64_t p = 0; p < n; p++) iperm[perm[p]] = (int32_t)p;

@@ -63,10 +63,18 @@ int validate_csr(int64_t n, int64_t nnz, const int64_t *rp, const int32_t *ci, c
 int ic_factor_host(int64_t n, const int64_t *rp, const int32_t *ci, const double *va, int lfil, double tau,
                    Factor &F, int64_t *bad_col);
 
-// perm[new] = old: rows cut into slabs of bsize consecutive rows of the
-// natural order; inside a slab, by level of L, then by row.  Every slab keeps
-// its position range, and P L P^T stays lower triangular.
-void slab_level_order(const Factor &F, int64_t bsize, std::vector<int32_t> &perm, std::vector<int32_t> &iperm);
+// Greedy multicolour ordering (nle_multicolor_order in nle.h): perm[new] =
+// old, rows by colour then by row.  Returns the number of colours.
+int32_t multicolor_order(int64_t n, const int64_t *rp, const int32_t *ci, int distance, std::vector<int32_t> &perm);
+// B = P A P^T (perm[new] = old) in CSR with ascending columns in every row.
+void permute_csr(int64_t n, const int64_t *rp, const int32_t *ci, const double *va, const std::vector<int32_t> &perm,
+                 std::vector<int64_t> &brp, std::vector<int32_t> &bci, std::vector<double> &bva);
+// perm[new] = old: rows cut into slabs of bsize consecutive values of
+// locality[row] (the row itself when locality is NULL; locality must be a
+// permutation of 0..n-1); inside a slab, by level of L, then by locality.
+// P L P^T stays lower triangular.
+void slab_level_order(const Factor &F, int64_t bsize, const int32_t *locality, std::vector<int32_t> &perm,
+                      std::vector<int32_t> &iperm);
 
 void permute(int64_t n, const int64_t *rp, const int32_t *ci, const double *va, const Factor &F,
              const std::vector<int32_t> &perm, const std::vector<int32_t> &iperm, int64_t npad, Permuted &P);

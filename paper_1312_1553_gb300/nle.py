@@ -22,6 +22,7 @@ STATUS = {0: "NLE_OK", 1: "NLE_ERR_ARG", 2: "NLE_ERR_CSR", 3: "NLE_ERR_NOT_SPD",
           5: "NLE_ERR_NOCONV", 6: "NLE_ERR_CUDA", 7: "NLE_ERR_OOM", 8: "NLE_ERR_TIMEOUT", 9: "NLE_ERR_STATE",
           10: "NLE_ERR_NO_DEVICE"}
 NLE_FP64, NLE_MIXED = 0, 1
+NLE_ORDER_NATURAL, NLE_ORDER_MULTICOLOR1, NLE_ORDER_MULTICOLOR2 = 0, 1, 2
 EXITS = ("tol", "maxit", "eigres", "stagnation", "breakdown")
 PHASES = ("spmv", "update", "fwd_solve", "bwd_solve", "dots", "direction", "outer_fp64", "other")
 NLE_MAX_P = 64
@@ -29,7 +30,7 @@ NLE_MAX_P = 64
 # every symbol include/nle.h declares
 EXPORTS = ("nle_default_options", "nle_create", "nle_factor_ic", "nle_solve", "nle_backward", "nle_batch_solve",
            "nle_apply_shifted", "nle_apply_prec", "nle_pcg", "nle_get_factor", "nle_last_error", "nle_destroy",
-           "nle_ic_apply_noalloc")
+           "nle_ic_apply_noalloc", "nle_multicolor_order")
 NLE_NOALLOC_MAX_N = 262144
 
 
@@ -38,7 +39,7 @@ class nle_options(ctypes.Structure):
                 ("max_dacg", ctypes.c_int), ("precision", ctypes.c_int), ("exit_eigres", ctypes.c_int),
                 ("exit_stagnation", ctypes.c_int), ("dacg_recompute", ctypes.c_int),
                 ("spin_timeout_s", ctypes.c_double), ("grid_ctas", ctypes.c_int), ("trsv_warps", ctypes.c_int),
-                ("spin_sleep_ns", ctypes.c_int)]
+                ("ordering", ctypes.c_int)]
 
 
 class nle_stats(ctypes.Structure):
@@ -85,6 +86,7 @@ def load_library(path: str = LIB_PATH):
         "nle_pcg": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_double, ctypes.c_int, _vp, ctypes.c_int, _vp,
                                    ctypes.c_int, _vp, _vp, _vp, ctypes.POINTER(nle_pcg_info), ctypes.c_int]),
         "nle_get_factor": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+        "nle_multicolor_order": (ctypes.c_int, [_i64, _vp, _vp, ctypes.c_int, _vp, _vp]),
         "nle_last_error": (ctypes.c_char_p, [_vp]),
         "nle_destroy": (None, [_vp]),
         "nle_ic_apply_noalloc": (ctypes.c_int, [_i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
@@ -152,6 +154,22 @@ def nle_apply_prec(h, k, S_ptr, R_ptr, m, Q_ptr, g_ptr, c_ptr, on_device) -> int
 def nle_pcg(h, theta, tol, max_pcg, r_ptr, m, Q_ptr, k, S_ptr, R_ptr, s_ptr, info: nle_pcg_info, on_device) -> int:
     return load_library().nle_pcg(h, float(theta), float(tol), int(max_pcg), r_ptr, int(m), Q_ptr, int(k), S_ptr,
                                   R_ptr, s_ptr, ctypes.byref(info), int(on_device))
+
+
+def nle_multicolor_order(n, rowptr_ptr, col_ptr, distance, perm_ptr, ncolors_ptr) -> int:
+    return _lib.nle_multicolor_order(n, rowptr_ptr, col_ptr, distance, perm_ptr, ncolors_ptr)
+
+
+def multicolor_order(A, distance: int = 2):
+    """(perm, ncolors) of nle_multicolor_order for a CSR with numpy arrays."""
+    rp = np.ascontiguousarray(A.rowptr, dtype=np.int64)
+    ci = np.ascontiguousarray(A.col, dtype=np.int32)
+    perm = np.zeros(int(A.n), np.int32)
+    nc = np.zeros(1, np.int32)
+    st = nle_multicolor_order(int(A.n), _hptr(rp), _hptr(ci), distance, _hptr(perm), _hptr(nc))
+    if st != NLE_OK:
+        raise NLEError(st, nle_last_error(None))
+    return perm, int(nc[0])
 
 
 def nle_get_factor(h, nnz_ptr, rp_ptr, col_ptr, val_ptr, levL_ptr, levU_ptr, nlevL_ptr, nlevU_ptr) -> int:

@@ -51,7 +51,8 @@ def main(names):
     for name in names:
         A, st = W.workload(name)
         p = st["p"]
-        opt = O.OracleOptions(tol=st["tol"], lfil=st["lfil"], tau_ic=st["tau_ic"])
+        opt = O.OracleOptions(tol=st["tol"], lfil=st["lfil"], tau_ic=st["tau_ic"],
+                              max_newton=st.get("max_newton", 100))
         X0 = W.start_vectors(A.n, p, st["seed"])
         t0 = time.time()
         lam, V, stats = O.dacg_newton(A, p, X0, opt)

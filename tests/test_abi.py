@@ -89,3 +89,46 @@ def test_csr_validation_without_device(lib, case):
         expect = 3
     st, h, msg = _create(W.CSR(6, rp, col, val))
     assert st == expect, msg
+
+
+@pytest.mark.parametrize("name", ["aniso2d_30x37", "diff3d7_24", "rgg3000", "hex27_16"])
+@pytest.mark.parametrize("distance", [1, 2])
+def test_multicolor_order_matches_reference_and_is_greedy(lib, name, distance):
+    """nle_multicolor_order (host C) equals the definition in workloads, and
+    the colouring it encodes is proper and greedy: no neighbour (distance 1
+    or 2) shares a row's colour, and every smaller colour is held by an
+    earlier neighbour."""
+    from paper_1312_1553_gb300 import nle
+
+    A, _ = W.workload(name)
+    perm, nc = nle.multicolor_order(A, distance)
+    ref, nc_ref, color = W.multicolor_order(A, distance, return_colors=True)
+    assert nc == nc_ref
+    np.testing.assert_array_equal(perm, ref)
+    assert np.array_equal(np.sort(perm), np.arange(A.n))
+    # perm lists the colours in order, rows ascending inside each
+    key = color[perm] * A.n + perm
+    assert np.all(np.diff(key) > 0)
+    S = A.to_scipy().tocsr()
+    S.data[:] = 1.0
+    G = (S @ S).tocsr() if distance == 2 else S
+    rng = W.rng_for(5)
+    for i in rng.choice(A.n, size=min(A.n, 300), replace=False):
+        nb = G.indices[G.indptr[i]:G.indptr[i + 1]]
+        nb = nb[nb != i]
+        assert not np.any(color[nb] == color[i]), i
+        earlier = set(color[nb[nb < i]].tolist())
+        assert set(range(color[i])) <= earlier, i
+
+
+def test_multicolor_order_argument_errors(lib):
+    from paper_1312_1553_gb300 import nle
+
+    A = W.tridiag(6)
+    with pytest.raises(nle.NLEError):
+        nle.multicolor_order(A, 3)
+    bad = W.CSR(A.n, A.rowptr.copy(), A.col.copy(), A.val.copy())
+    bad.col[3] = 99
+    with pytest.raises(nle.NLEError) as e:
+        nle.multicolor_order(bad, 1)
+    assert e.value.args and "column" in str(e.value)

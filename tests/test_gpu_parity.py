@@ -258,6 +258,41 @@ def test_solve_matches_oracle(nle, name, prec):
 
 
 @pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("name", ["diff3d7_24", "diff2d5_60x70", "rgg3000", "hex27_16"])
+def test_multicolor_ordering_matches_oracle_on_permuted_matrix(nle, name, prec):
+    """nle_options.ordering = NLE_ORDER_MULTICOLOR2: the library factors
+    P A P^T with P from the greedy distance-2 colouring, the oracle runs the
+    same method on workloads.permute(A, perm).  Factor and levels bit-exact;
+    eigenvalues and eigenvectors (returned in the caller's numbering) against
+    the oracle's, mapped back through perm."""
+    A, st = load(name)
+    perm, ncolors = W.multicolor_order(A, 2)
+    B = W.permute(A, perm)
+    p = st["p"]
+    X0 = W.start_vectors(A.n, p, st["seed"])
+    s = solver(nle, A, prec, ordering=nle.NLE_ORDER_MULTICOLOR2)
+    s.factor_ic(st["lfil"], st["tau_ic"])
+    F = s.get_factor()
+    ic = O.ic_factor(B, st["lfil"], st["tau_ic"])
+    np.testing.assert_array_equal(F["Lrowptr"], ic.Lrowptr)
+    np.testing.assert_array_equal(F["Lcol"], ic.Lcol)
+    np.testing.assert_array_equal(F["Lval"].view(np.uint64), ic.Lval.view(np.uint64))
+    np.testing.assert_array_equal(F["levL"], ic.levL)
+    assert F["nlevL"] == ic.nlevL
+    lam, V, stats = s.solve(p, st["tol"], 100, 20, X0)
+    lam = lam.cpu().numpy()
+    V = V.cpu().numpy()
+    s.close()
+    opt = O.OracleOptions(tol=st["tol"], lfil=st["lfil"], tau_ic=st["tau_ic"])
+    lref, Vref, _ = O.dacg_newton(B, p, X0[:, perm], opt, ic=ic)
+    np.testing.assert_allclose(lam, lref, rtol=1e-10 if prec == "fp64" else 1e-8)
+    for j in range(p):
+        assert sin_angle(V[j][perm], Vref[:, j]) <= 1e-6
+    _check_solution(A, lam, V, st["tol"])
+    assert all(stats["converged"]) and stats["ascending"]
+
+
+@pytest.mark.parametrize("prec", PRECS)
 def test_solve_full_size_100cubed(nle, prec):
     """n = 1e6, p = 10, IC(10, 1e-3), tol 1e-8: eigenvalues against the stored
     oracle run, eigenvector samples, residuals and orthogonality at full size."""
@@ -298,11 +333,12 @@ def test_solve_full_size_hex27_96(nle):
     X0 = W.start_vectors(A.n, p, st["seed"])
     s = solver(nle, A, "mixed")
     s.factor_ic(st["lfil"], st["tau_ic"])
-    lam_t, V_t, stats = s.solve(p, st["tol"], 100, 20, X0)
+    lam_t, V_t, stats = s.solve(p, st["tol"], st["max_newton"], 20, X0)
     grad = s.backward(torch.ones(p, dtype=torch.float64), None).cpu().numpy()
     s.close()
     lam = lam_t.cpu().numpy()
     V = V_t.cpu().numpy()
+    assert all(gold["oracle_stats"]["converged"])
     glam = np.array(gold["lam"])
     np.testing.assert_allclose(lam, glam, rtol=1e-8)
     gaps = np.minimum(np.diff(glam, prepend=-np.inf), np.diff(glam, append=np.inf))
