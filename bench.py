@@ -17,6 +17,7 @@ recurrence) and rank 0 prints the line.
 from __future__ import annotations
 
 import argparse
+import ctypes
 import hashlib
 import json
 import os
@@ -79,6 +80,36 @@ def cpu_sample(workload: str, npairs: int) -> dict:
     lam, V, stats = O.dacg_newton(A, npairs, X0, opt, ic=ic)
     sec = time.perf_counter() - t0
     return dict(seconds=sec, eigenpairs=npairs, lam=[float(x) for x in lam])
+
+
+BATCH = "graph_batch"
+BATCH_P = 4
+BATCH_SAMPLE = 10  # problems of the batch timed on the oracle (at most ~25 s)
+
+
+def batch_problem_start(A, b: int):
+    import workloads as W
+
+    return W.start_vectors(A.n, BATCH_P, W.BASE_SEED + 400 + b)
+
+
+def cpu_sample_batch() -> dict:
+    """The oracle, as it stands, on the first problems of the batched
+    workload (up to BATCH_SAMPLE problems or about 25 s)."""
+    import oracle as O
+    import workloads as W
+
+    mats = W.graph_batch(count=BATCH_SAMPLE)
+    sec, pairs = 0.0, 0
+    for b, A in enumerate(mats):
+        ic = O.ic_factor(A, 30, 1e-2)
+        t0 = time.perf_counter()
+        O.dacg_newton(A, BATCH_P, batch_problem_start(A, b), O.OracleOptions(tol=1e-8, lfil=30, tau_ic=1e-2), ic=ic)
+        sec += time.perf_counter() - t0
+        pairs += BATCH_P
+        if sec > 25.0:
+            break
+    return dict(seconds=sec, eigenpairs=pairs, problems=pairs // BATCH_P)
 
 
 def run_cpu_sample(workload: str, npairs: int) -> dict:
@@ -230,10 +261,131 @@ def peak_hbm():
 # our arm
 # ---------------------------------------------------------------------------
 
+def batch_main(args, world, rank, local, cpu):
+    """Batched workload: 256 grounded geometric-graph Laplacians, p = 4 each,
+    solved by one nle_batch_solve per step (one persistent launch, groups
+    of 4 CTAs taking problems from a device queue)."""
+    import torch
+
+    import workloads as W
+    from paper_1312_1553_gb300 import _build, nle
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    _build.build()
+    nle.load_library()
+    mats = W.graph_batch(count=256)
+    prec = nle.NLE_MIXED if args.precision == "mixed" else nle.NLE_FP64
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        t0 = time.perf_counter()
+        solvers = []
+        for A in mats:
+            s = nle.Eigensolver(A, dict(precision=prec, grid_ctas=4), stream=stream)
+            s.factor_ic(30, 1e-2)
+            solvers.append(s)
+        ic_seconds = time.perf_counter() - t0
+        nnz_l = [int(s.get_factor()["Lrowptr"][-1]) for s in solvers]
+        X0h = [torch.tensor(batch_problem_start(A, b), dtype=torch.float64).pin_memory() for b, A in enumerate(mats)]
+        X0d = [x.to("cuda") for x in X0h]
+        count = len(solvers)
+        H = (ctypes.c_void_p * count)(*[s.h.value for s in solvers])
+        lams = [torch.empty(BATCH_P, dtype=torch.float64, device="cuda") for _ in solvers]
+        Vs = [torch.empty((BATCH_P, s.n), dtype=torch.float64, device="cuda") for s in solvers]
+        L = (ctypes.c_void_p * count)(*[t.data_ptr() for t in lams])
+        V = (ctypes.c_void_p * count)(*[t.data_ptr() for t in Vs])
+        X = (ctypes.c_void_p * count)(*[t.data_ptr() for t in X0d])
+        per = (ctypes.c_int * count)()
+
+        def step():
+            rc = nle.nle_batch_solve(count, H, BATCH_P, 1e-8, 100, 20, X, L, V, per)
+            if rc != 0:
+                raise nle.NLEError(rc, nle.nle_last_error(solvers[0].h))
+
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        clk = ClockSampler(local)
+        clk.start()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        ms_kernel = 0.0
+        for _ in range(args.steps):
+            step()
+            ms_kernel += solvers[0].last_stats()["ms_batch"]
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        clocks = clk.stop()
+        ms = ev0.elapsed_time(ev1)
+        stats = [s.last_stats() for s in solvers]
+        # end to end: start vectors from pinned host memory in, eigenvalues out
+        lam_h = torch.empty((count, BATCH_P), dtype=torch.float64).pin_memory()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        if not args.skip_e2e:
+            for _ in range(args.steps):
+                for b in range(count):
+                    X0d[b].copy_(X0h[b], non_blocking=True)
+                step()
+                for b in range(count):
+                    lam_h[b].copy_(lams[b], non_blocking=True)
+                torch.cuda.synchronize()
+        e2e_sec = max(time.perf_counter() - t0, 1e-9)
+        for s in solvers:
+            s.close()
+    t_max, e2e_max = ms / 1000.0, e2e_sec
+    if world > 1:
+        tt = torch.tensor([t_max, e2e_max], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_max, e2e_max = float(tt[0]), float(tt[1])
+    if args.skip_e2e:
+        e2e_max = float("inf")
+    pairs = count * BATCH_P
+    w = 4 if prec == nle.NLE_MIXED else 8
+    b_step = sum(alg_bytes(A.n, A.nnz, nl, w, st["pcg_iterations"], st["pcg_sum_m"], st["pcg_sum_k"], "pcg") +
+                 alg_bytes(A.n, A.nnz, nl, w, st["dacg_iterations"], st["dacg_sum_m"], 0, "dacg")
+                 for A, nl, st in zip(mats, nnz_l, stats))
+    ms_launch = ms_kernel / args.steps
+    peak, peak_kind = peak_hbm()
+    achieved = (b_step / 1e9) / (ms_launch / 1e3)
+    line = dict(metric=f"eigenpairs/s, {count} graph Laplacians batched, rel. residual 1e-8",
+                value=world * pairs * args.steps / t_max, unit=UNIT, n_gpus=world, steps=args.steps,
+                warmup=args.warmup, ms_per_step=1000 * t_max / args.steps, higher_is_better=True, scaling="weak",
+                vs_baseline=None, dtype="f32" if prec == nle.NLE_MIXED else "f64", data="synthetic",
+                config=dict(workload=f"{BATCH}: {count} random geometric graph Laplacians + 1e-3 I, "
+                                     f"n ~ U[2000, 60000], p = {BATCH_P}",
+                            n_total=sum(A.n for A in mats), nnz_total=sum(A.nnz for A in mats), lfil=30, tau_ic=1e-2,
+                            tol=1e-8, ic_seconds=ic_seconds, l2="working set > 129 MB L2 (no flush needed)",
+                            parallelism=f"replicas{world}" if world > 1 else "single GPU, groups of 4 CTAs"),
+                roofline=dict(bound="hbm", achieved=achieved, peak=peak, unit="GB/s", frac=achieved / peak,
+                              traffic=load_traffic("k_batch"), kernel="k_batch",
+                              peak_source=f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)" if peak_kind == "measured"
+                              else "fallback 6.8 TB/s", alg_bytes_per_launch=b_step, ms_per_launch=ms_launch),
+                cpu_baseline=cpu,
+                e2e=None if args.skip_e2e else dict(
+                    value=world * pairs * args.steps / e2e_max, unit=UNIT,
+                    h2d_bytes_per_step=sum(x.numel() * 8 for x in X0h), d2h_bytes_per_step=count * BATCH_P * 8),
+                clocks=clocks, gpu_launches=args.steps * (1 + count * (BATCH_P + 1)),
+                iterations=dict(pcg=sum(st["pcg_iterations"] for st in stats),
+                                dacg=sum(st["dacg_iterations"] for st in stats)))
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
 def main():
     args = parse()
     if args.cpu_sample:
-        print(json.dumps(cpu_sample(args.workload, args.sample_eigenpairs)))
+        print(json.dumps(cpu_sample_batch() if args.workload == BATCH else
+                         cpu_sample(args.workload, args.sample_eigenpairs)))
         return 0
     if args.impl == "reference":
         return reference_arm(args)
@@ -248,9 +400,17 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
-            cpu = cpu_baseline_entry(run_cpu_sample(args.workload, CPU_SAMPLE_PAIRS), args.workload)
+            if args.workload == BATCH:
+                r = run_cpu_sample(BATCH, 0)
+                cpu = dict(value=r["eigenpairs"] / r["seconds"], unit=UNIT, cores=1, kind="oracle",
+                           sample=f"oracle (numpy + plain C, FP64, 1 thread) on problems 1-{r['problems']} of the "
+                                  f"batch, p = {BATCH_P} each ({r['seconds']:.1f} s, IC set-up excluded)")
+            else:
+                cpu = cpu_baseline_entry(run_cpu_sample(args.workload, CPU_SAMPLE_PAIRS), args.workload)
         except Exception as e:  # reported, not fatal
             cpu = dict(value=None, unit=UNIT, cores=1, kind="oracle", sample=f"failed: {e}")
+    if args.workload == BATCH:
+        return batch_main(args, world, rank, local, cpu)
 
     import numpy as np
     import torch

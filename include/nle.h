@@ -135,6 +135,8 @@ typedef struct {
                                    backward solve, dot products, direction, outer FP64 step,
                                    other (Gram matrices) */
   int ascending;                /* 1 when eigenvalues came out strictly ascending */
+  double ms_batch;              /* device time of the batched launch that solved this
+                                   problem (nle_batch_solve; 0 after nle_solve) */
 } nle_stats;
 
 /* Parameters and outcome of one inner solve (nle_pcg). */
@@ -222,6 +224,12 @@ nle_status nle_backward(nle_t h, const double *gbar_lambda, const double *gbar_V
 nle_status nle_batch_solve(int count, nle_t *hs, int p, double tol, int max_newton, int max_pcg,
                            const double *const *X0s, double *const *lambdas, double *const *Vs,
                            nle_status *per_problem);
+
+/* Statistics of the handle's last solve, by nle_solve or as one problem of
+ * nle_batch_solve (there the device times of the phases are 0 and ms_batch
+ * is the time of the whole batched launch).  NLE_ERR_STATE before any
+ * solve. */
+nle_status nle_get_stats(nle_t h, nle_stats *stats);
 
 /* ---- Building blocks of the hot path, exposed for verification ---------- */
 

@@ -198,6 +198,8 @@ struct nle_ctx {
   std::string err;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   float last_batch_ms = 0.f;  // device time of the last nle_batch_solve led by this handle
+  nle_stats last_stats{};     // statistics of the last solve (single or batched)
+  bool has_stats = false;
 };
 
 static thread_local std::string g_create_error;
@@ -551,7 +553,7 @@ nle_status nle_factor_ic(nle_t h, int lfil, double tau_ic) {
   const size_t tsz = mixed(h) ? 4 : 8;
   if (mixed(h)) {
     SellSet<float> S;
-    build_sell<float>(P, H, h->bsize, S);
+    build_sell<float>(P, H, h->bsize, !P0.empty(), S);
     NLE_CUDA(h, upload(h->A_sptr, S.A.sptr));
     NLE_CUDA(h, upload(h->A_col, S.A.col));
     NLE_CUDA(h, upload(h->A_val, S.A.val));
@@ -569,7 +571,7 @@ nle_status nle_factor_ic(nle_t h, int lfil, double tau_ic) {
     NLE_CUDA(h, upload(h->d_diag, S.diag));
   } else {
     SellSet<double> S;
-    build_sell<double>(P, H, h->bsize, S);
+    build_sell<double>(P, H, h->bsize, !P0.empty(), S);
     NLE_CUDA(h, upload(h->A_sptr, S.A.sptr));
     NLE_CUDA(h, upload(h->A_col, S.A.col));
     NLE_CUDA(h, upload(h->A_val, S.A.val));
@@ -624,6 +626,36 @@ nle_status nle_get_factor(nle_t h, int64_t *nnzL, int64_t *Lrowptr, int32_t *Lco
 // ---------------------------------------------------------------------------
 // solve
 // ---------------------------------------------------------------------------
+// Per-solve statistics from the device state of one problem.
+static void fill_stats(const State &st, int p, double ms_dacg, double ms_newton, int64_t launches, double ms_batch,
+                       nle_stats *stats) {
+  memset(stats, 0, sizeof(*stats));
+  stats->p = p;
+  bool asc = true;
+  for (int j = 0; j < p; j++) {
+    stats->dacg_its[j] = st.dacg_its[j];
+    stats->outer_its[j] = st.outer_its[j];
+    stats->pcg_its[j] = st.pcg_its[j];
+    stats->converged[j] = st.conv[j];
+    stats->final_res[j] = st.res[j];
+    if (j > 0 && !(st.lambda[j] > st.lambda[j - 1])) asc = false;
+  }
+  stats->mvp_dacg = st.mvp_dacg;
+  stats->mvp_newton = st.mvp_newton;
+  for (int e = 0; e < 5; e++) stats->exit_count[e] = st.exits[e];
+  stats->ms_dacg = ms_dacg;
+  stats->ms_newton = ms_newton;
+  stats->pcg_iterations = st.pcg_total;
+  stats->pcg_sum_m = st.pcg_sum_m;
+  stats->pcg_sum_k = st.pcg_sum_k;
+  stats->dacg_iterations = st.dacg_total;
+  stats->dacg_sum_m = st.dacg_sum_m;
+  stats->kernel_launches = launches;
+  for (int q = 0; q < 8; q++) stats->ms_phase[q] = st.tphase[q] * 1e-6;
+  stats->ascending = asc ? 1 : 0;
+  stats->ms_batch = ms_batch;
+}
+
 template <typename T>
 static nle_status solve_impl(nle_t h, int p, double tol, int max_newton, int max_pcg, const double *X0,
                              double *lambda, double *V, nle_stats *stats, int on_dev) {
@@ -684,36 +716,19 @@ static nle_status solve_impl(nle_t h, int p, double tol, int max_newton, int max
   h->lambda.assign(st.lambda, st.lambda + p);
   h->solved = true;
   h->last_p = p;
-  bool allconv = true, asc = true;
-  for (int j = 0; j < p; j++) {
-    allconv = allconv && st.conv[j];
-    if (j > 0 && !(st.lambda[j] > st.lambda[j - 1])) asc = false;
-  }
-  if (stats) {
-    memset(stats, 0, sizeof(*stats));
-    stats->p = p;
-    for (int j = 0; j < p; j++) {
-      stats->dacg_its[j] = st.dacg_its[j];
-      stats->outer_its[j] = st.outer_its[j];
-      stats->pcg_its[j] = st.pcg_its[j];
-      stats->converged[j] = st.conv[j];
-      stats->final_res[j] = st.res[j];
-    }
-    stats->mvp_dacg = st.mvp_dacg;
-    stats->mvp_newton = st.mvp_newton;
-    for (int e = 0; e < 5; e++) stats->exit_count[e] = st.exits[e];
-    stats->ms_dacg = ms_dacg;
-    stats->ms_newton = ms_newton;
-    stats->pcg_iterations = st.pcg_total;
-    stats->pcg_sum_m = st.pcg_sum_m;
-    stats->pcg_sum_k = st.pcg_sum_k;
-    stats->dacg_iterations = st.dacg_total;
-    stats->dacg_sum_m = st.dacg_sum_m;
-    stats->kernel_launches = launches;
-    for (int q = 0; q < 8; q++) stats->ms_phase[q] = st.tphase[q] * 1e-6;
-    stats->ascending = asc ? 1 : 0;
-  }
+  bool allconv = true;
+  for (int j = 0; j < p; j++) allconv = allconv && st.conv[j];
+  fill_stats(st, p, ms_dacg, ms_newton, launches, 0.0, &h->last_stats);
+  h->has_stats = true;
+  if (stats) *stats = h->last_stats;
   if (!allconv) return fail(h, NLE_ERR_NOCONV, "some eigenpairs reached max_newton");
+  return NLE_OK;
+}
+
+extern "C" nle_status nle_get_stats(nle_t h, nle_stats *stats) {
+  if (!h || !stats) return fail(h, NLE_ERR_ARG, "NULL argument");
+  if (!h->has_stats) return fail(h, NLE_ERR_STATE, "no solve has run on this handle");
+  *stats = h->last_stats;
   return NLE_OK;
 }
 
@@ -998,6 +1013,8 @@ static nle_status batch_impl(int count, nle_t *hs, int p, double tol, int max_ne
       h->last_p = p;
       h->solved = true;
     }
+    fill_stats(st, p, 0.0, 0.0, 0, ms, &h->last_stats);
+    h->has_stats = true;
     if (per_problem) per_problem[b] = s;
     if (s != NLE_OK && (worst == NLE_OK || worst == NLE_ERR_NOCONV)) worst = s;
   }

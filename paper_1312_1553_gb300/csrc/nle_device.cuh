@@ -334,11 +334,16 @@ __device__ __forceinline__ void sell_rows(const Sell<TV> &M, const TX *__restric
 // The wait is warp-uniform: the warp re-polls the entries still missing
 // until every lane holds its values (a vote), then reduces with shuffles; a
 // per-lane wait followed by the warp's reconvergence measured about 1.5x
-// slower per dependency hop.  Rows of a group that depend on each other are
-// done in rounds (round[r] = longest chain to r inside its group,
-// precomputed) separated by __syncwarp, so a lane never waits for a lane of
-// its own warp.  Every wait is bounded; since every warp and CTA is resident
-// (cooperative launch) and works in dependency order, every wait ends.
+// slower per dependency hop.  The rows of a group are done in rounds
+// separated by __syncwarp (round[r] precomputed), so a lane never waits for
+// a lane of its own warp.  The rows of one round publish together, so a
+// round waits for the inputs of all of them; every wait ends when each
+// round's inputs come from strictly earlier levels (or, in the slab order of
+// the natural ordering, from earlier positions of the same slab or from
+// lower slabs only).  Natural order: round[r] = longest dependency chain to
+// r inside its group.  Slabs whose dependencies can point to later slabs
+// (the multicolour ordering): one level per round.  Every wait is also
+// bounded in time; every warp and CTA is resident (cooperative launch).
 template <typename T>
 struct TriEll {
   const int64_t *off;    // per slab: first entry

@@ -342,7 +342,8 @@ static void pack(int64_t n, int64_t npad, int H, const std::vector<int64_t> &rp,
 // (lower: earlier rows of the group; upper: later rows).
 template <typename TV>
 static void ell(int64_t n, int64_t npad, int64_t bsize, bool lower, const std::vector<int64_t> &rp,
-                const std::vector<int32_t> &col, const std::vector<double> &val, EllHost<TV> &out) {
+                const std::vector<int32_t> &col, const std::vector<double> &val, const std::vector<int32_t> *lev,
+                EllHost<TV> &out) {
   const int64_t ns = (npad + bsize - 1) / bsize;
   out.off.assign(ns + 1, 0);
   out.width.assign(ns, 8);
@@ -367,7 +368,20 @@ static void ell(int64_t n, int64_t npad, int64_t bsize, bool lower, const std::v
   out.round.assign(npad, 0);
   for (int64_t g0 = 0; g0 < n; g0 += 4) {
     const int64_t g1 = std::min(n, g0 + 4);
-    if (lower) {
+    if (lev) {
+      // one level per round: rank of the row's level among the group's
+      // levels, ascending for L, descending for L^T
+      for (int64_t r = g0; r < g1; r++) {
+        int rank = 0;
+        for (int64_t t = g0; t < g1; t++) {
+          bool below = lower ? (*lev)[t] < (*lev)[r] : (*lev)[t] > (*lev)[r];
+          for (int64_t u = g0; u < t && below; u++)
+            if ((*lev)[u] == (*lev)[t]) below = false;  // count each level once
+          rank += below;
+        }
+        out.round[r] = (uint8_t)rank;
+      }
+    } else if (lower) {
       for (int64_t r = g0; r < g1; r++)
         for (int64_t e = rp[r]; e < rp[r + 1]; e++)
           if (col[e] >= g0) out.round[r] = std::max<uint8_t>(out.round[r], out.round[col[e]] + 1);
@@ -380,17 +394,18 @@ static void ell(int64_t n, int64_t npad, int64_t bsize, bool lower, const std::v
 }
 
 template <typename TV>
-void build_sell(const Permuted &P, int H, int64_t bsize, SellSet<TV> &S) {
+void build_sell(const Permuted &P, int H, int64_t bsize, bool level_rounds, SellSet<TV> &S) {
   pack<TV>(P.n, P.npad, H, P.Arp, P.Acol, P.Aval, 0, 0, S.A);
   pack<double>(P.n, P.npad, H, P.Arp, P.Acol, P.Aval, 0, 0, S.A64);
-  ell<TV>(P.n, P.npad, bsize, true, P.Lrp, P.Lcol, P.Lval, S.L);
-  ell<TV>(P.n, P.npad, bsize, false, P.Urp, P.Ucol, P.Uval, S.U);
+  const std::vector<int32_t> *lev = level_rounds ? &P.lev : nullptr;
+  ell<TV>(P.n, P.npad, bsize, true, P.Lrp, P.Lcol, P.Lval, lev, S.L);
+  ell<TV>(P.n, P.npad, bsize, false, P.Urp, P.Ucol, P.Uval, lev, S.U);
   S.diag.assign(P.npad, TV(1));
   for (int64_t i = 0; i < P.n; i++) S.diag[i] = TV(P.diag[i]);
 }
 
-template void build_sell<float>(const Permuted &, int, int64_t, SellSet<float> &);
-template void build_sell<double>(const Permuted &, int, int64_t, SellSet<double> &);
+template void build_sell<float>(const Permuted &, int, int64_t, bool, SellSet<float> &);
+template void build_sell<double>(const Permuted &, int, int64_t, bool, SellSet<double> &);
 
 void permute(int64_t n, const int64_t *rp, const int32_t *ci, const double *va, const Factor &F,
              const std::vector<int32_t> &perm, const std::vector<int32_t> &iperm, int64_t npad, Permuted &P) {

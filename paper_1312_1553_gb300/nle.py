@@ -30,7 +30,7 @@ NLE_MAX_P = 64
 # every symbol include/nle.h declares
 EXPORTS = ("nle_default_options", "nle_create", "nle_factor_ic", "nle_solve", "nle_backward", "nle_batch_solve",
            "nle_apply_shifted", "nle_apply_prec", "nle_pcg", "nle_get_factor", "nle_last_error", "nle_destroy",
-           "nle_ic_apply_noalloc", "nle_multicolor_order")
+           "nle_ic_apply_noalloc", "nle_multicolor_order", "nle_get_stats")
 NLE_NOALLOC_MAX_N = 262144
 
 
@@ -50,7 +50,8 @@ class nle_stats(ctypes.Structure):
                 ("ms_newton", ctypes.c_double), ("ms_pcg_inner", ctypes.c_double),
                 ("pcg_iterations", ctypes.c_int64), ("pcg_sum_m", ctypes.c_int64), ("pcg_sum_k", ctypes.c_int64),
                 ("dacg_iterations", ctypes.c_int64), ("dacg_sum_m", ctypes.c_int64),
-                ("kernel_launches", ctypes.c_int64), ("ms_phase", ctypes.c_double * 8), ("ascending", ctypes.c_int)]
+                ("kernel_launches", ctypes.c_int64), ("ms_phase", ctypes.c_double * 8), ("ascending", ctypes.c_int),
+                ("ms_batch", ctypes.c_double)]
 
 
 class nle_pcg_info(ctypes.Structure):
@@ -87,6 +88,7 @@ def load_library(path: str = LIB_PATH):
                                    ctypes.c_int, _vp, _vp, _vp, ctypes.POINTER(nle_pcg_info), ctypes.c_int]),
         "nle_get_factor": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
         "nle_multicolor_order": (ctypes.c_int, [_i64, _vp, _vp, ctypes.c_int, _vp, _vp]),
+        "nle_get_stats": (ctypes.c_int, [_vp, ctypes.POINTER(nle_stats)]),
         "nle_last_error": (ctypes.c_char_p, [_vp]),
         "nle_destroy": (None, [_vp]),
         "nle_ic_apply_noalloc": (ctypes.c_int, [_i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
@@ -154,6 +156,10 @@ def nle_apply_prec(h, k, S_ptr, R_ptr, m, Q_ptr, g_ptr, c_ptr, on_device) -> int
 def nle_pcg(h, theta, tol, max_pcg, r_ptr, m, Q_ptr, k, S_ptr, R_ptr, s_ptr, info: nle_pcg_info, on_device) -> int:
     return load_library().nle_pcg(h, float(theta), float(tol), int(max_pcg), r_ptr, int(m), Q_ptr, int(k), S_ptr,
                                   R_ptr, s_ptr, ctypes.byref(info), int(on_device))
+
+
+def nle_get_stats(h, stats: nle_stats) -> int:
+    return _lib.nle_get_stats(h, ctypes.byref(stats))
 
 
 def nle_multicolor_order(n, rowptr_ptr, col_ptr, distance, perm_ptr, ncolors_ptr) -> int:
@@ -272,6 +278,12 @@ class Eigensolver:
         self._check(st, allow=(5,) if allow_noconv else ())
         return lam, V, stats_dict(stats)
 
+    def last_stats(self) -> dict:
+        """Statistics of the last solve on this handle (single or batched)."""
+        st = nle_stats()
+        self._check(nle_get_stats(self.h, st))
+        return stats_dict(st)
+
     def backward(self, gbar_lambda=None, gbar_V=None, grad=None):
         """Accumulate dL/dA_e for every stored entry e into grad (created as
         zeros when None) for the last solve; gbar_V is (p, n)."""
@@ -351,7 +363,8 @@ def stats_dict(s: nle_stats) -> dict:
                 ms_newton=float(s.ms_newton), pcg_iterations=int(s.pcg_iterations), pcg_sum_m=int(s.pcg_sum_m),
                 pcg_sum_k=int(s.pcg_sum_k), dacg_iterations=int(s.dacg_iterations), dacg_sum_m=int(s.dacg_sum_m),
                 kernel_launches=int(s.kernel_launches),
-                ms_phase=dict(zip(PHASES, [float(x) for x in s.ms_phase])), ascending=bool(s.ascending))
+                ms_phase=dict(zip(PHASES, [float(x) for x in s.ms_phase])), ascending=bool(s.ascending),
+                ms_batch=float(s.ms_batch))
 
 
 def _eigsh_function():

@@ -31,8 +31,16 @@ def test_batch_matches_single_and_oracle(nle, prec):
         s.factor_ic(30, 1e-2)
         solvers.append(s)
         X0s.append(W.start_vectors(A.n, p, 700 + i))
+    with pytest.raises(nle.NLEError) as e:
+        solvers[0].last_stats()
+    assert e.value.code == 9  # NLE_ERR_STATE: nothing solved yet
     lams, Vs, per = nle.batch_solve(solvers, p, 1e-8, 100, 20, X0s)
     assert all(x == 0 for x in per), per
+    for s in solvers:
+        st = s.last_stats()
+        assert st["p"] == p and all(st["converged"]) and st["ascending"]
+        assert st["pcg_iterations"] > 0 and st["dacg_iterations"] > 0 and st["ms_batch"] > 0
+        assert st["pcg_iterations"] == sum(st["pcg_its"])
     rtol = 1e-8 if prec == "mixed" else 1e-10
     for i, A in enumerate(mats):
         lam = lams[i].cpu().numpy()
