@@ -55,6 +55,9 @@ def parse():
     ap.add_argument("--trsv-warps", type=int, default=0, help="0 = library default")
     ap.add_argument("--ordering", default="natural", choices=["natural", "mc1", "mc2"],
                     help="symmetric ordering before the IC factor (natural = the paper's)")
+    ap.add_argument("--bfgs", default="simplified", choices=["simplified", "full"],
+                    help="BFGS update of the preconditioner (simplified = the paper's eq. lastprec)")
+    ap.add_argument("--max-newton", type=int, default=100, help="outer step cap (the paper's ITMAX = 100)")
     ap.add_argument("--spin-timeout", type=float, default=0.0, help="0 = library default (seconds)")
     ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--sample-eigenpairs", type=int, default=1, help=argparse.SUPPRESS)
@@ -301,8 +304,8 @@ def batch_main(args, world, rank, local, cpu):
         per = (ctypes.c_int * count)()
 
         def step():
-            rc = nle.nle_batch_solve(count, H, BATCH_P, 1e-8, 100, 20, X, L, V, per)
-            if rc != 0:
+            rc = nle.nle_batch_solve(count, H, BATCH_P, 1e-8, args.max_newton, 20, X, L, V, per)
+            if rc not in (0, 5):  # 5 = NLE_ERR_NOCONV: counted below, outputs written
                 raise nle.NLEError(rc, nle.nle_last_error(solvers[0].h))
 
         for _ in range(args.warmup):
@@ -324,6 +327,7 @@ def batch_main(args, world, rank, local, cpu):
         clocks = clk.stop()
         ms = ev0.elapsed_time(ev1)
         stats = [s.last_stats() for s in solvers]
+        unconverged = [b for b in range(count) if per[b] != 0]
         # end to end: start vectors from pinned host memory in, eigenvalues out
         lam_h = torch.empty((count, BATCH_P), dtype=torch.float64).pin_memory()
         torch.cuda.synchronize()
@@ -373,7 +377,10 @@ def batch_main(args, world, rank, local, cpu):
                     h2d_bytes_per_step=sum(x.numel() * 8 for x in X0h), d2h_bytes_per_step=count * BATCH_P * 8),
                 clocks=clocks, gpu_launches=args.steps * (1 + count * (BATCH_P + 1)),
                 iterations=dict(pcg=sum(st["pcg_iterations"] for st in stats),
-                                dacg=sum(st["dacg_iterations"] for st in stats)))
+                                dacg=sum(st["dacg_iterations"] for st in stats)),
+                unconverged=dict(problems=len(unconverged), max_newton=args.max_newton,
+                                 detail=[dict(problem=b, n=mats[b].n, outer_its=stats[b]["outer_its"],
+                                              final_res=stats[b]["final_res"]) for b in unconverged[:8]]))
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -428,6 +435,7 @@ def main():
 
     A, st = W.workload(args.workload)
     p = args.pairs if args.pairs > 0 else st["p"]
+    max_newton = max(args.max_newton, st.get("max_newton", 100))
     X0 = W.start_vectors(A.n, p, st["seed"])
     prec = nle.NLE_MIXED if args.precision == "mixed" else nle.NLE_FP64
     opts = dict(precision=prec)
@@ -437,6 +445,7 @@ def main():
         opts["spin_timeout_s"] = args.spin_timeout
     opts["ordering"] = {"natural": nle.NLE_ORDER_NATURAL, "mc1": nle.NLE_ORDER_MULTICOLOR1,
                         "mc2": nle.NLE_ORDER_MULTICOLOR2}[args.ordering]
+    opts["bfgs_update"] = nle.NLE_BFGS_FULL if args.bfgs == "full" else nle.NLE_BFGS_SIMPLIFIED
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         s = nle.Eigensolver(A, opts, stream=stream)
@@ -451,7 +460,7 @@ def main():
 
         def step():
             stats = nle.nle_stats()
-            rc = nle.nle_solve(s.h, p, st["tol"], 100, 20, nle._dptr(x0), nle._dptr(lam), nle._dptr(V), stats, 1)
+            rc = nle.nle_solve(s.h, p, st["tol"], max_newton, 20, nle._dptr(x0), nle._dptr(lam), nle._dptr(V), stats, 1)
             if rc != 0:
                 raise nle.NLEError(rc, nle.nle_last_error(s.h))
             return nle.stats_dict(stats)
@@ -482,7 +491,7 @@ def main():
         t0 = time.perf_counter()
         for _ in range(0 if args.skip_e2e else args.steps):
             stats = nle.nle_stats()
-            rc = nle.nle_solve(s.h, p, st["tol"], 100, 20, nle._dptr(x0_h), nle._dptr(lam_h), nle._dptr(V_h),
+            rc = nle.nle_solve(s.h, p, st["tol"], max_newton, 20, nle._dptr(x0_h), nle._dptr(lam_h), nle._dptr(V_h),
                                stats, 0)
             if rc != 0:
                 raise nle.NLEError(rc, nle.nle_last_error(s.h))
@@ -532,7 +541,7 @@ def main():
                 config=dict(workload=f"{args.workload}: {DESCRIPTION.get(args.workload, args.workload)}",
                             n=A.n, nnz=A.nnz, p=p, lfil=st["lfil"], tau_ic=st["tau_ic"], tol=st["tol"],
                             precision="FP32 bulk + FP64 outer step" if prec == nle.NLE_MIXED else "FP64",
-                            nnz_L=nnz_l, nlev_L=F["nlevL"], ordering=args.ordering, ic_seconds=ic_seconds,
+                            nnz_L=nnz_l, nlev_L=F["nlevL"], ordering=args.ordering, bfgs=args.bfgs, ic_seconds=ic_seconds,
                             l2="working set > 129 MB L2 (no flush needed)",
                             parallelism=f"replicas{world}" if world > 1 else "single GPU"),
                 roofline=roof, cpu_baseline=cpu,

@@ -99,7 +99,17 @@ typedef struct {
   int trsv_warps;        /* warps per CTA in the triangular solves, 1..16 (default 16) */
   int ordering;          /* NLE_ORDER_NATURAL (default) or a multicolour ordering, see
                             nle_multicolor_order; applied before the IC factor */
+  int bfgs_update;       /* NLE_BFGS_SIMPLIFIED (default) or NLE_BFGS_FULL */
 } nle_options;
+
+/* BFGS update of the preconditioner (Section 3).  The full update uses
+ * y_k = r_{k+1} - r_k; the paper's simplified update (eq. "lastprec", the
+ * one its experiments use) replaces y_k by -r_k.  Either way Algorithm 3.1
+ * runs on the stored pairs (s_k, w_k), w_k = -y_k, and a pair is kept only
+ * when s_k^T w_k < 0 (Theorem 3.2).  The full update needs k_max <=
+ * NLE_MAX_KMAX - 1 (one slot stages the newest pair until r_{k+1} is known). */
+#define NLE_BFGS_SIMPLIFIED 0
+#define NLE_BFGS_FULL 1
 
 /* Symmetric orderings applied by nle_factor_ic before the IC factor.  The
  * paper factors A as given; a multicolour ordering factors P A P^T instead

@@ -55,6 +55,10 @@ class OracleOptions:
     tau_ic: float = 1e-2
     exit_eigres: bool = True  # exit (iii)
     exit_stagnation: bool = True  # exit (iv)
+    # Section 3: the full BFGS update uses y_k = r_{k+1} - r_k; the default is
+    # the simplified update (eq. "lastprec") with y_k replaced by -r_k.  Both
+    # store the pair (s_k, w_k) with w_k = -y_k and apply Algorithm 3.1 to it.
+    bfgs_full: bool = False
     debug_exact_eigres: bool = False  # also compute exit (iii) with an extra MVP
 
 
@@ -300,23 +304,27 @@ def dacg_newton(A, p: int, X0: np.ndarray, opt: OracleOptions, ic=None):
             if Qt.shape[1]:
                 u_new = u_new - Qt @ (Qt.T @ u_new)
                 u_new = u_new / np.linalg.norm(u_new)
-            # Theorem 3.2: the update keeps Phat SPD when alpha = s^T r < 0,
-            # which holds when the correction equation is solved; a pair
-            # with alpha >= 0 (e.g. s = 0 after an immediate PCG breakdown)
-            # defines no SPD update and is not stored.
-            if opt.k_max > 0 and s @ r < 0:
+            u = u_new
+            Au = _ic.spmv(A, u)
+            mvp_n += 1
+            theta = u @ Au
+            r_new = Au - theta * u
+            # the pair's second vector: w = -y with y = r_{k+1} - r_k (full
+            # update) or y ~ -r_k (simplified, eq. "lastprec")
+            w = r - r_new if opt.bfgs_full else r
+            # Theorem 3.2: the update keeps Phat SPD when alpha = s^T w < 0
+            # (s^T y > 0), which holds when the correction equation is
+            # solved; a pair with alpha >= 0 (e.g. s = 0 after an immediate
+            # PCG breakdown) defines no SPD update and is not stored.
+            if opt.k_max > 0 and s @ w < 0:
                 if len(S) == opt.k_max:
                     S.pop(0)
                     R.pop(0)
                     alpha.pop(0)
                 S.append(s)
-                R.append(r)
-                alpha.append(s @ r)
-            u = u_new
-            Au = _ic.spmv(A, u)
-            mvp_n += 1
-            theta = u @ Au
-            r = Au - theta * u
+                R.append(w)
+                alpha.append(s @ w)
+            r = r_new
             k += 1
         lam[j] = theta
         stats["outer_its"].append(k)
@@ -325,6 +333,7 @@ def dacg_newton(A, p: int, X0: np.ndarray, opt: OracleOptions, ic=None):
         stats["newton_mvp"].append(mvp_n)
         stats["converged"].append(bool(np.linalg.norm(r) <= opt.tol * theta))
         stats["final_res"].append(float(np.linalg.norm(r) / theta))
+        stats["last_pairs"] = (list(S), list(R))
         Qt = np.concatenate([Qt, u[:, None]], axis=1)
     V = np.stack([fix_sign(Qt[:, j]) for j in range(p)], axis=1)
     stats["ascending"] = bool(np.all(np.diff(lam) > 0))

@@ -312,6 +312,7 @@ static Opts make_opts(nle_t h, double tol, int max_newton, int max_pcg) {
   O.recompute = h->opt.dacg_recompute;
   O.spin_ns = (long long)(h->opt.spin_timeout_s * 1e9);
   O.trsv_warps = h->opt.trsv_warps;
+  O.bfgs_full = h->opt.bfgs_update == NLE_BFGS_FULL ? 1 : 0;
   return O;
 }
 
@@ -403,6 +404,7 @@ void nle_default_options(nle_options *o) {
   o->grid_ctas = 0;
   o->trsv_warps = 16;
   o->ordering = NLE_ORDER_NATURAL;
+  o->bfgs_update = NLE_BFGS_SIMPLIFIED;
 }
 
 const char *nle_last_error(nle_t h) { return h ? h->err.c_str() : g_create_error.c_str(); }
@@ -433,6 +435,10 @@ nle_status nle_create(int64_t n, int64_t nnz, const int64_t *rowptr, const int32
   if (h->opt.trsv_warps < 1 || h->opt.trsv_warps > NWARP) return fail(nullptr, NLE_ERR_ARG, "trsv_warps out of range");
   if (h->opt.ordering < NLE_ORDER_NATURAL || h->opt.ordering > NLE_ORDER_MULTICOLOR2)
     return fail(nullptr, NLE_ERR_ARG, "unknown ordering");
+  if (h->opt.bfgs_update != NLE_BFGS_SIMPLIFIED && h->opt.bfgs_update != NLE_BFGS_FULL)
+    return fail(nullptr, NLE_ERR_ARG, "unknown bfgs_update");
+  if (h->opt.bfgs_update == NLE_BFGS_FULL && h->opt.k_max > NLE_MAX_KMAX - 1)
+    return fail(nullptr, NLE_ERR_ARG, "the full BFGS update keeps one slot for the newest pair: k_max <= NLE_MAX_KMAX - 1");
   h->n = n;
   h->nnz = nnz;
   h->rowptr.resize(n + 1);

@@ -87,6 +87,7 @@ struct Opts {
   int recompute;
   long long spin_ns;
   int trsv_warps;     // warps per CTA that take part in the triangular solves
+  int bfgs_full;      // 1: pairs (s_k, r_k - r_{k+1}) (full BFGS update), 0: (s_k, r_k)
 };
 
 // Pointers handed to the persistent kernels (by value).

@@ -536,12 +536,15 @@ __device__ bool fp64_rayleigh(const Dev<T> &D, Shared &sh, Ctl &ctl, const doubl
   return reduce_all(D, sh, ctl, 2, 40);
 }
 
-// r = Au - theta u, ||r||^2 in sh.sc[0]; shadows rT and Q[:, j] = u.
+// r = A u - theta u (FP64, and its working-precision copy rT), ||r||^2 in
+// sh.sc[0]; shadows Q[:, j] = u.  With stage >= 0 (full BFGS update) the staged pair's second vector, which
+// holds r_k, becomes w = r_k - r_{k+1} and sc[1] = s^T w.
 template <typename T, int RPC>
-__device__ bool fp64_residual(const Dev<T> &D, Shared &sh, Ctl &ctl, const double *u, double theta, int j) {
+__device__ bool fp64_residual(const Dev<T> &D, Shared &sh, Ctl &ctl, const double *u, double theta, int j,
+                              int stage = -1) {
   constexpr int W = VT<T>::W;
   const int64_t tid = gtid(), TT = gthreads();
-  double rr = 0.0;
+  double rr = 0.0, sw = 0.0;
   T *uq = D.Q + (int64_t)j * D.npad;
 #pragma unroll
   for (int i = 0; i < RPC; i++) {
@@ -561,10 +564,22 @@ __device__ bool fp64_residual(const Dev<T> &D, Shared &sh, Ctl &ctl, const doubl
       stv(D.r + ch * W, rv);
       stv(D.rT + ch * W, rt);
       stv(uq + ch * W, ut);
+      if (stage >= 0) {
+        T sv[W], wv[W];
+        ldc(D.S + (int64_t)stage * D.npad + ch * W, sv);
+        ldc(D.R + (int64_t)stage * D.npad + ch * W, wv);
+#pragma unroll
+        for (int v = 0; v < W; v++) {
+          wv[v] = T(double(wv[v]) - rv[v]);
+          sw += double(sv[v]) * double(wv[v]);
+        }
+        stv(D.R + (int64_t)stage * D.npad + ch * W, wv);
+      }
     }
   }
   red_put(sh, 0, rr);
-  return reduce_all(D, sh, ctl, 1, 41);
+  if (stage >= 0) red_put(sh, 1, sw);
+  return reduce_all(D, sh, ctl, stage >= 0 ? 2 : 1, 41);
 }
 
 template <typename T>
@@ -602,6 +617,7 @@ __device__ bool newton_body(const Dev<T> &D, const Opts &O, Shared &sh, Ctl &ctl
   const int m = j + 1;
   double *u = D.Qt + (int64_t)j * D.npad;
   int k = 0;  // pairs reset for every eigenpair
+  int spare = O.kmax;  // full update: physical slot staging the newest pair
   if (threadIdx.x == 0)
     for (int s = 0; s < KMAX; s++) sh.order[s] = s;
   __syncthreads();
@@ -627,9 +643,14 @@ __device__ bool newton_body(const Dev<T> &D, const Opts &O, Shared &sh, Ctl &ctl
     sum_m += (long long)po.its * m;
     sum_k += (long long)po.its * k;
     exits[po.exit]++;
-    // store the pair (s_k, r_k) when alpha < 0 (Theorem 3.2); ring of k_max
-    int slot = -1;
-    if (O.kmax > 0 && po.rs < 0.0) {
+    // simplified update: store the pair (s_k, r_k) when alpha = s^T r_k < 0
+    // (Theorem 3.2) in the ring of k_max slots.  Full update: copy (s_k, r_k)
+    // into the spare slot; it becomes (s_k, r_k - r_{k+1}) with the next
+    // residual and joins the ring if s^T w < 0.
+    int slot = -1, stage = -1;
+    if (O.kmax > 0 && O.bfgs_full) {
+      stage = spare;
+    } else if (O.kmax > 0 && po.rs < 0.0) {
       if (k < O.kmax) {
         slot = k;
         if (threadIdx.x == 0) sh.order[k] = k;
@@ -645,6 +666,7 @@ __device__ bool newton_body(const Dev<T> &D, const Opts &O, Shared &sh, Ctl &ctl
       }
     }
     __syncthreads();
+    const int wslot = slot >= 0 ? slot : stage;
     // N1: t = u + s (FP64); copy the pair; ||t||^2, Qt^T t
     double tv[RPC][W];
     {
@@ -662,11 +684,11 @@ __device__ bool newton_body(const Dev<T> &D, const Opts &O, Shared &sh, Ctl &ctl
             tv[i][v] = uv[v] + double(sv[v]);
             tt += tv[i][v] * tv[i][v];
           }
-          if (slot >= 0) {
+          if (wslot >= 0) {
             T rt[W];
             ldc(D.rT + ch * W, rt);
-            stv(D.S + (int64_t)slot * D.npad + ch * W, sv);
-            stv(D.R + (int64_t)slot * D.npad + ch * W, rt);
+            stv(D.S + (int64_t)wslot * D.npad + ch * W, sv);
+            stv(D.R + (int64_t)wslot * D.npad + ch * W, rt);
           }
         } else {
 #pragma unroll
@@ -725,8 +747,31 @@ __device__ bool newton_body(const Dev<T> &D, const Opts &O, Shared &sh, Ctl &ctl
     if (!fp64_rayleigh<T, RPC>(D, sh, ctl, u)) return false;
     mvp++;
     theta = sh.sc[0] / sh.sc[1];
-    if (!fp64_residual<T, RPC>(D, sh, ctl, u, theta, j)) return false;
+    if (!fp64_residual<T, RPC>(D, sh, ctl, u, theta, j, stage)) return false;
     rnorm = sqrt(sh.sc[0]);
+    if (stage >= 0 && sh.sc[1] < 0.0) {
+      // the staged pair joins the ring; the slot it replaces (or the lowest
+      // free one) becomes the spare
+      if (k < O.kmax) {
+        if (threadIdx.x == 0) sh.order[k] = stage;
+        k++;
+        __syncthreads();
+        for (spare = 0;; spare++) {
+          bool used = false;
+          for (int s = 0; s < k; s++) used = used || sh.order[s] == spare;
+          if (!used) break;
+        }
+      } else {
+        const int evicted = sh.order[0];
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          for (int s = 0; s + 1 < k; s++) sh.order[s] = sh.order[s + 1];
+          sh.order[k - 1] = stage;
+        }
+        spare = evicted;
+      }
+      __syncthreads();
+    }
     tmark(sh, PH_OUTER);
     it++;
   }

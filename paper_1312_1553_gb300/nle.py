@@ -23,6 +23,7 @@ STATUS = {0: "NLE_OK", 1: "NLE_ERR_ARG", 2: "NLE_ERR_CSR", 3: "NLE_ERR_NOT_SPD",
           10: "NLE_ERR_NO_DEVICE"}
 NLE_FP64, NLE_MIXED = 0, 1
 NLE_ORDER_NATURAL, NLE_ORDER_MULTICOLOR1, NLE_ORDER_MULTICOLOR2 = 0, 1, 2
+NLE_BFGS_SIMPLIFIED, NLE_BFGS_FULL = 0, 1
 EXITS = ("tol", "maxit", "eigres", "stagnation", "breakdown")
 PHASES = ("spmv", "update", "fwd_solve", "bwd_solve", "dots", "direction", "outer_fp64", "other")
 NLE_MAX_P = 64
@@ -39,7 +40,7 @@ class nle_options(ctypes.Structure):
                 ("max_dacg", ctypes.c_int), ("precision", ctypes.c_int), ("exit_eigres", ctypes.c_int),
                 ("exit_stagnation", ctypes.c_int), ("dacg_recompute", ctypes.c_int),
                 ("spin_timeout_s", ctypes.c_double), ("grid_ctas", ctypes.c_int), ("trsv_warps", ctypes.c_int),
-                ("ordering", ctypes.c_int)]
+                ("ordering", ctypes.c_int), ("bfgs_update", ctypes.c_int)]
 
 
 class nle_stats(ctypes.Structure):

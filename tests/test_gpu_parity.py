@@ -293,6 +293,32 @@ def test_multicolor_ordering_matches_oracle_on_permuted_matrix(nle, name, prec):
 
 
 @pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("name", ["aniso2d_30x37", "diff3d7_24", "rgg3000"])
+def test_full_bfgs_update_matches_oracle(nle, name, prec):
+    """nle_options.bfgs_update = NLE_BFGS_FULL (Section 3, y_k = r_{k+1} -
+    r_k) against the oracle run with the same update."""
+    A, st = load(name)
+    p = st["p"]
+    X0 = W.start_vectors(A.n, p, st["seed"])
+    s = solver(nle, A, prec, bfgs_update=nle.NLE_BFGS_FULL)
+    s.factor_ic(st["lfil"], st["tau_ic"])
+    lam, V, stats = s.solve(p, st["tol"], 100, 20, X0)
+    lam = lam.cpu().numpy()
+    V = V.cpu().numpy()
+    s.close()
+    opt = O.OracleOptions(tol=st["tol"], lfil=st["lfil"], tau_ic=st["tau_ic"], bfgs_full=True)
+    lref, Vref, rstats = O.dacg_newton(A, p, X0, opt)
+    np.testing.assert_allclose(lam, lref, rtol=1e-10 if prec == "fp64" else 1e-8)
+    for j in range(p):
+        assert sin_angle(V[j], Vref[:, j]) <= (1e-8 if st["tol"] <= 1e-10 else 1e-6)
+    _check_solution(A, lam, V, st["tol"])
+    assert all(stats["converged"]) and stats["ascending"]
+    if prec == "fp64":
+        # same pairs, same decisions: the outer step counts agree with the oracle's
+        assert stats["outer_its"] == rstats["outer_its"]
+
+
+@pytest.mark.parametrize("prec", PRECS)
 def test_solve_full_size_100cubed(nle, prec):
     """n = 1e6, p = 10, IC(10, 1e-3), tol 1e-8: eigenvalues against the stored
     oracle run, eigenvector samples, residuals and orthogonality at full size."""

@@ -555,3 +555,27 @@ def test_kappa_gradient_fd_and_euler_identity():
         km.flat[c] -= h
         fd = (loss_of(kp)[0] - loss_of(km)[0]) / (2 * h)
         assert abs(fd - gk.flat[c]) <= 1e-6 * scale, (c, fd, gk.flat[c])
+
+
+def test_full_bfgs_update_pairs_and_closed_form():
+    """Section 3's full BFGS update (y_k = r_{k+1} - r_k): the method still
+    reaches the closed-form spectrum of the anisotropic Laplacian; every
+    stored pair has alpha = s^T w < 0 (Theorem 3.2, SPD update); and the
+    preconditioner built from the stored pairs maps -w_k to s_k for the
+    newest pair (the secant condition P_{k+1} y_k = s_k)."""
+    A, st = W.workload("aniso2d_30x37")
+    p = 3
+    X0 = W.start_vectors(A.n, p, st["seed"])
+    opt = O.OracleOptions(tol=1e-10, lfil=st["lfil"], tau_ic=st["tau_ic"], bfgs_full=True)
+    ic = O.ic_factor(A, st["lfil"], st["tau_ic"])
+    lam, V, stats = O.dacg_newton(A, p, X0, opt, ic=ic)
+    exact = W.laplacian_2d_aniso_eigs(30, 37, 1.0, 1.7)[:p]
+    np.testing.assert_allclose(lam, exact, rtol=1e-10)
+    S, R = stats["last_pairs"]
+    assert len(S) >= 1
+    for s, w in zip(S, R):
+        assert s @ w < 0
+    # secant: the update that appended the newest pair maps -w to s
+    alpha = [s @ w for s, w in zip(S, R)]
+    c = O.bfgs_apply(-R[-1], S, R, alpha, ic, None)
+    np.testing.assert_allclose(c, S[-1], rtol=1e-9, atol=1e-12 * np.linalg.norm(S[-1]))
