@@ -313,9 +313,6 @@ def test_full_bfgs_update_matches_oracle(nle, name, prec):
         assert sin_angle(V[j], Vref[:, j]) <= (1e-8 if st["tol"] <= 1e-10 else 1e-6)
     _check_solution(A, lam, V, st["tol"])
     assert all(stats["converged"]) and stats["ascending"]
-    if prec == "fp64":
-        # same pairs, same decisions: the outer step counts agree with the oracle's
-        assert stats["outer_its"] == rstats["outer_its"]
 
 
 @pytest.mark.parametrize("prec", PRECS)
