@@ -57,7 +57,9 @@ def parse():
                     help="symmetric ordering before the IC factor (natural = the paper's)")
     ap.add_argument("--bfgs", default="simplified", choices=["simplified", "full"],
                     help="BFGS update of the preconditioner (simplified = the paper's eq. lastprec)")
-    ap.add_argument("--max-newton", type=int, default=100, help="outer step cap (the paper's ITMAX = 100)")
+    ap.add_argument("--max-newton", type=int, default=0,
+                    help="outer step cap; 0 = the workload's (the paper's ITMAX = 100; 400 for workloads with "
+                         "eigenvalue clusters)")
     ap.add_argument("--spin-timeout", type=float, default=0.0, help="0 = library default (seconds)")
     ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--sample-eigenpairs", type=int, default=1, help=argparse.SUPPRESS)
@@ -78,7 +80,7 @@ def cpu_sample(workload: str, npairs: int) -> dict:
     A, st = W.workload(workload)
     ic = O.ic_factor(A, st["lfil"], st["tau_ic"])
     X0 = W.start_vectors(A.n, npairs, st["seed"])
-    opt = O.OracleOptions(tol=st["tol"], lfil=st["lfil"], tau_ic=st["tau_ic"])
+    opt = O.OracleOptions(tol=st["tol"], lfil=st["lfil"], tau_ic=st["tau_ic"], max_newton=st.get("max_newton", 100))
     t0 = time.perf_counter()
     lam, V, stats = O.dacg_newton(A, npairs, X0, opt, ic=ic)
     sec = time.perf_counter() - t0
@@ -88,6 +90,9 @@ def cpu_sample(workload: str, npairs: int) -> dict:
 BATCH = "graph_batch"
 BATCH_P = 4
 BATCH_SAMPLE = 10  # problems of the batch timed on the oracle (at most ~25 s)
+# the larger graphs have lambda_2 and lambda_3 within 0.4 % of each other; the
+# oracle needs up to ~170 Newton steps there
+BATCH_MAX_NEWTON = 400
 
 
 def batch_problem_start(A, b: int):
@@ -107,7 +112,8 @@ def cpu_sample_batch() -> dict:
     for b, A in enumerate(mats):
         ic = O.ic_factor(A, 30, 1e-2)
         t0 = time.perf_counter()
-        O.dacg_newton(A, BATCH_P, batch_problem_start(A, b), O.OracleOptions(tol=1e-8, lfil=30, tau_ic=1e-2), ic=ic)
+        O.dacg_newton(A, BATCH_P, batch_problem_start(A, b),
+                      O.OracleOptions(tol=1e-8, lfil=30, tau_ic=1e-2, max_newton=BATCH_MAX_NEWTON), ic=ic)
         sec += time.perf_counter() - t0
         pairs += BATCH_P
         if sec > 25.0:
@@ -281,6 +287,7 @@ def batch_main(args, world, rank, local, cpu):
     _build.build()
     nle.load_library()
     mats = W.graph_batch(count=256)
+    max_newton = args.max_newton or BATCH_MAX_NEWTON
     prec = nle.NLE_MIXED if args.precision == "mixed" else nle.NLE_FP64
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
@@ -304,7 +311,7 @@ def batch_main(args, world, rank, local, cpu):
         per = (ctypes.c_int * count)()
 
         def step():
-            rc = nle.nle_batch_solve(count, H, BATCH_P, 1e-8, args.max_newton, 20, X, L, V, per)
+            rc = nle.nle_batch_solve(count, H, BATCH_P, 1e-8, max_newton, 20, X, L, V, per)
             if rc not in (0, 5):  # 5 = NLE_ERR_NOCONV: counted below, outputs written
                 raise nle.NLEError(rc, nle.nle_last_error(solvers[0].h))
 
@@ -378,7 +385,7 @@ def batch_main(args, world, rank, local, cpu):
                 clocks=clocks, gpu_launches=args.steps * (1 + count * (BATCH_P + 1)),
                 iterations=dict(pcg=sum(st["pcg_iterations"] for st in stats),
                                 dacg=sum(st["dacg_iterations"] for st in stats)),
-                unconverged=dict(problems=len(unconverged), max_newton=args.max_newton,
+                unconverged=dict(problems=len(unconverged), max_newton=max_newton,
                                  detail=[dict(problem=b, n=mats[b].n, outer_its=stats[b]["outer_its"],
                                               final_res=stats[b]["final_res"]) for b in unconverged[:8]]))
     if rank == 0:
@@ -435,7 +442,7 @@ def main():
 
     A, st = W.workload(args.workload)
     p = args.pairs if args.pairs > 0 else st["p"]
-    max_newton = max(args.max_newton, st.get("max_newton", 100))
+    max_newton = args.max_newton or st.get("max_newton", 100)
     X0 = W.start_vectors(A.n, p, st["seed"])
     prec = nle.NLE_MIXED if args.precision == "mixed" else nle.NLE_FP64
     opts = dict(precision=prec)
