@@ -219,11 +219,12 @@ nle_status nle_backward(nle_t h, const double *gbar_lambda, const double *gbar_V
                         int buffers_on_device);
 
 /* Solve `count` independent problems (each handle factored) in ONE
- * persistent launch: groups of 4 CTAs take problems from a device work
+ * persistent launch: groups of G CTAs take problems from a device work
  * queue, largest n first, and each group runs the whole of Algorithm 3.2
  * (DACG and Newton for every eigenpair) for its problem, then takes the next.
- * Requirements: every handle was factored for at most 4 CTAs (create it with
- * nle_options.grid_ctas = 4, or small enough n), all handles share the
+ * G = 4, or 8 when some handle was factored for more than 4 CTAs.
+ * Requirements: every handle was factored for at most 8 CTAs (create it with
+ * nle_options.grid_ctas = 4 or 8, or small enough n), all handles share the
  * precision and the device; the options of hs[0] apply and the work runs on
  * hs[0]'s stream.  p, tol, max_newton, max_pcg as in nle_solve.
  * lambdas[b] [p] and Vs[b] [p*n_b] are device pointers; X0s may be NULL or

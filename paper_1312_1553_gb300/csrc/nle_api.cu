@@ -932,7 +932,10 @@ static nle_status batch_impl(int count, nle_t *hs, int p, double tol, int max_ne
                              const double *const *X0s, double *const *lambdas, double *const *Vs,
                              nle_status *per_problem) {
   nle_t h0 = hs[0];
-  constexpr int G = 4;  // CTAs per group
+  // CTAs per group: 4, or 8 when some handle was factored for more than 4
+  int G = 4;
+  for (int b = 0; b < count; b++)
+    if (hs[b]->grid > 4) G = 8;
   int rpc = 1;
   size_t dyn = 0;
   std::vector<Dev<T>> devs(count);
@@ -1037,8 +1040,8 @@ extern "C" nle_status nle_batch_solve(int count, nle_t *hs, int p, double tol, i
     if (!hs[b]->factored) return fail(hs[b], NLE_ERR_STATE, "nle_factor_ic has not been called");
     if (hs[b]->opt.precision != hs[0]->opt.precision || hs[b]->device != hs[0]->device)
       return fail(hs[b], NLE_ERR_ARG, "all handles of a batch need the same precision and device");
-    if (hs[b]->grid > 4)
-      return fail(hs[b], NLE_ERR_ARG, "batched handles must be factored for at most 4 CTAs (nle_options.grid_ctas <= 4)");
+    if (hs[b]->grid > 8)
+      return fail(hs[b], NLE_ERR_ARG, "batched handles must be factored for at most 8 CTAs (nle_options.grid_ctas <= 8)");
     if (p < 1 || p >= hs[b]->n || p > NLE_MAX_P || !lambdas[b] || !Vs[b])
       return fail(hs[b], NLE_ERR_ARG, "bad p or output pointer");
   }

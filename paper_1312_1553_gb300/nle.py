@@ -333,7 +333,7 @@ class Eigensolver:
 
 
 def batch_solve(solvers, p: int, tol: float, max_newton: int = 100, max_pcg: int = 20, X0s=None):
-    """nle_batch_solve over Eigensolver objects (created with grid_ctas <= 4).
+    """nle_batch_solve over Eigensolver objects (created with grid_ctas <= 8).
     Returns (lambdas, Vs, statuses): lists of CUDA tensors and status codes."""
     import torch
 

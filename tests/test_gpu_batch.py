@@ -59,12 +59,41 @@ def test_batch_matches_single_and_oracle(nle, prec):
 
 
 def test_batch_rejects_wide_layout(nle):
-    """A handle factored for more than 4 CTAs cannot join a batch (its slab
+    """A handle factored for more than 8 CTAs cannot join a batch (its slab
     layout is tied to its CTA count)."""
     B = W.geometric_graph_laplacian(40000, 6)  # 10,000 row groups: 20 CTAs wanted
-    s = nle.Eigensolver(B, dict(precision=nle.NLE_MIXED, grid_ctas=8))
+    s = nle.Eigensolver(B, dict(precision=nle.NLE_MIXED, grid_ctas=16))
     s.factor_ic(30, 1e-2)
     with pytest.raises(nle.NLEError) as e:
         nle.batch_solve([s], 2, 1e-8)
     assert e.value.code == 1
     s.close()
+
+
+def test_batch_groups_of_eight_fp64(nle):
+    """A handle factored for 8 CTAs (FP64, n = 36,000) makes the batch run in
+    groups of 8; every problem matches its single-problem solve, the
+    smallest also the oracle."""
+    sizes = [36000, 2600, 4100]
+    mats = [W.geometric_graph_laplacian(n, 950 + i) for i, n in enumerate(sizes)]
+    p = 3
+    solvers, X0s = [], []
+    for i, A in enumerate(mats):
+        s = nle.Eigensolver(A, dict(precision=nle.NLE_FP64, grid_ctas=8))
+        s.factor_ic(30, 1e-2)
+        solvers.append(s)
+        X0s.append(W.start_vectors(A.n, p, 720 + i))
+    lams, Vs, per = nle.batch_solve(solvers, p, 1e-8, 400, 20, X0s)
+    assert all(x == 0 for x in per), per
+    for i, A in enumerate(mats):
+        lam = lams[i].cpu().numpy()
+        l1, V1, _ = solvers[i].solve(p, 1e-8, 400, 20, X0s[i])
+        np.testing.assert_allclose(lam, l1.cpu().numpy(), rtol=1e-10)
+        Asp = A.to_scipy()
+        V = Vs[i].cpu().numpy()
+        for j in range(p):
+            assert np.linalg.norm(Asp @ V[j] - lam[j] * V[j]) <= 1.5e-8 * lam[j]
+    lref, _, _ = O.dacg_newton(mats[1], p, X0s[1], O.OracleOptions(tol=1e-8, lfil=30, tau_ic=1e-2, max_newton=400))
+    np.testing.assert_allclose(lams[1].cpu().numpy(), lref, rtol=1e-10)
+    for s in solvers:
+        s.close()
