@@ -540,9 +540,9 @@ nle_status nle_factor_ic(nle_t h, int lfil, double tau_ic) {
   if (!rpc) return fail(h, NLE_ERR_ARG, "n too large for one persistent grid");
   h->grid = grid;
   h->rpc = rpc;
-  // one slab of rows per CTA in the triangular solves (a multiple of 4 rows,
+  // one slab of rows per CTA in the triangular solves (a multiple of TRSV_ROWS rows,
   // staged in shared memory)
-  h->bsize = ((h->npad + 4 * grid - 1) / (4 * grid)) * 4;
+  h->bsize = ((h->npad + TRSV_ROWS * grid - 1) / (TRSV_ROWS * grid)) * TRSV_ROWS;
   if (h->bsize * (int64_t)(mixed(h) ? 4 : 8) > 160 * 1024)
     return fail(h, NLE_ERR_ARG, "n too large for the shared-memory slab of one persistent grid");
   // with a multicolour ordering the slabs still follow the caller's row

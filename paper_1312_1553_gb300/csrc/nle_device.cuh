@@ -327,8 +327,9 @@ __device__ __forceinline__ void sell_rows(const Sell<TV> &M, const TX *__restric
 //
 // Each slab stores its rows in ELL form (width = the slab's longest row,
 // rounded up to 8), so the address of a row's entries follows from the row
-// index without a dependent load.  A warp takes four consecutive rows at a
-// time, 8 lanes per row, two entries per lane in flight, and fetches the
+// index without a dependent load.  A warp takes TRSV_ROWS consecutive rows
+// at a time, 32 / TRSV_ROWS lanes per row, 16 entries of each row in flight,
+// and fetches the
 // next group's entries, right-hand sides and pivots (as reciprocals, so no
 // division sits on the dependency chain) before the current group waits.
 // The wait is warp-uniform: the warp re-polls the entries still missing
@@ -351,13 +352,13 @@ struct TriEll {
   const int32_t *col;    // -1 = padding
   const T *val;
   const T *diag;          // npad
-  const uint8_t *round;   // npad: round of the row inside its group of 4
+  const uint8_t *round;   // npad: round of the row inside its group of TRSV_ROWS rows
 };
 
 template <typename T>
 struct TriPre {
-  int c0, c1;
-  T a0, a1;
+  int c[TRSV_EPL];  // columns of the lane's first entries (-1: none)
+  T a[TRSV_EPL];
   T rhs, rdg;  // right-hand side and 1 / pivot (lane g == 0 of each row)
   int rnd;
 };
@@ -366,15 +367,16 @@ template <bool LOWER, typename T, typename RHS>
 __device__ __forceinline__ void trsv_fetch(const TriEll<T> &M, int64_t b0, int64_t base, int wd, int64_t ngrp,
                                            int64_t it, int q, int g, RHS &rhs_of, TriPre<T> &P) {
   const int64_t gi = LOWER ? it : ngrp - 1 - it;
-  const int64_t r = b0 + 4 * gi + q;
+  const int64_t r = b0 + TRSV_ROWS * gi + q;
   const int64_t e = base + (r - b0) * wd + g;
-  P.c0 = __ldg(M.col + e);
-  P.a0 = __ldg(M.val + e);
-  P.c1 = -1;
-  P.a1 = T(0);
-  if (g + 8 < wd) {
-    P.c1 = __ldg(M.col + e + 8);
-    P.a1 = __ldg(M.val + e + 8);
+#pragma unroll
+  for (int k = 0; k < TRSV_EPL; k++) {
+    P.c[k] = -1;
+    P.a[k] = T(0);
+    if (g + k * TRSV_LANES < wd) {
+      P.c[k] = __ldg(M.col + e + k * TRSV_LANES);
+      P.a[k] = __ldg(M.val + e + k * TRSV_LANES);
+    }
   }
   P.rnd = __ldg(M.round + r);
   P.rhs = T(0);
@@ -393,27 +395,35 @@ __device__ __forceinline__ T trsv_peek(const T *x, const volatile T *stage, int6
 }
 
 // Warp-uniform wait: returns once every lane of the warp holds values (not
-// the marker) for its entries c0 and c1 (c < 0: no entry).  The clock is
-// read only after 2^20 rounds of polling; past spin_ns the wait records
+// the marker) for its N entries c[k] (c < 0: no entry).  The clock is read
+// only after 2^20 rounds of polling; past spin_ns the wait records
 // NLE_ERR_TIMEOUT and substitutes 0 so that dependants still finish.
-template <typename T>
-__device__ __forceinline__ void trsv_wait(const T *x, const volatile T *stage, int64_t b0, int64_t b1, int c0, int c1,
-                                          T &v0, T &v1, State *st, long long spin_ns) {
-  bool ok = !(c0 >= 0 && is_sent(v0)) && !(c1 >= 0 && is_sent(v1));
+template <int N, typename T>
+__device__ __forceinline__ void trsv_wait(const T *x, const volatile T *stage, int64_t b0, int64_t b1, const int *c,
+                                          T *v, State *st, long long spin_ns) {
+  auto ready = [&]() {
+    bool ok = true;
+#pragma unroll
+    for (int k = 0; k < N; k++) ok = ok && !(c[k] >= 0 && is_sent(v[k]));
+    return ok;
+  };
+  bool ok = ready();
   if (__all_sync(0xffffffffu, ok)) return;
   long long t0 = 0;
-  for (int k = 0;; k++) {
-    if (c0 >= 0 && is_sent(v0)) v0 = trsv_peek(x, stage, b0, b1, c0);
-    if (c1 >= 0 && is_sent(v1)) v1 = trsv_peek(x, stage, b0, b1, c1);
-    ok = !(c0 >= 0 && is_sent(v0)) && !(c1 >= 0 && is_sent(v1));
+  for (int it = 0;; it++) {
+#pragma unroll
+    for (int k = 0; k < N; k++)
+      if (c[k] >= 0 && is_sent(v[k])) v[k] = trsv_peek(x, stage, b0, b1, c[k]);
+    ok = ready();
     if (__all_sync(0xffffffffu, ok)) return;
-    if (k >= (1 << 20)) {
-      if (k == (1 << 20)) t0 = clock64();
+    if (it >= (1 << 20)) {
+      if (it == (1 << 20)) t0 = clock64();
       const bool late = clock64() - t0 > spin_ns * 21 / 10;  // cycles at about 2.1 GHz
       if (__any_sync(0xffffffffu, late)) {
         if (!ok) record_error(st, 8 /*NLE_ERR_TIMEOUT*/, 102);
-        if (c0 >= 0 && is_sent(v0)) v0 = T(0);
-        if (c1 >= 0 && is_sent(v1)) v1 = T(0);
+#pragma unroll
+        for (int k = 0; k < N; k++)
+          if (c[k] >= 0 && is_sent(v[k])) v[k] = T(0);
         return;
       }
     }
@@ -431,10 +441,10 @@ __device__ __forceinline__ void trsv_block(const TriEll<T> &M, T *x, int64_t npa
   for (int64_t i = threadIdx.x; i < nb; i += blockDim.x) stage[i] = sent;
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t ngrp = nb >> 2;
+  const int64_t ngrp = nb / TRSV_ROWS;
   int64_t it = warp;
   if (warp < twarps && it < ngrp) {
-    const int q = lane >> 3, g = lane & 7;
+    const int q = lane / TRSV_LANES, g = lane % TRSV_LANES;
     const int64_t base = __ldg(M.off + grank());
     const int wd = __ldg(M.width + grank());
     TriPre<T> cur, nxt;
@@ -445,34 +455,39 @@ __device__ __forceinline__ void trsv_block(const TriEll<T> &M, T *x, int64_t npa
       // the next group's entries and right-hand sides load while this one waits
       if (more) trsv_fetch<LOWER, T>(M, b0, base, wd, ngrp, itn, q, g, rhs_of, nxt);
       const int64_t gi = LOWER ? it : ngrp - 1 - it;
-      const int64_t r = b0 + 4 * gi + q;
+      const int64_t r = b0 + TRSV_ROWS * gi + q;
       const int rounds = 1 + __reduce_max_sync(0xffffffffu, (unsigned)cur.rnd);
       for (int rd = 0; rd < rounds; rd++) {
         const bool active = (cur.rnd == rd);
-        const int c0 = active ? cur.c0 : -1, c1 = active ? cur.c1 : -1;
-        T v0 = T(0), v1 = T(0);
-        if (c0 >= 0) v0 = trsv_peek(x, stage, b0, b1, c0);
-        if (c1 >= 0) v1 = trsv_peek(x, stage, b0, b1, c1);
-        trsv_wait(x, stage, b0, b1, c0, c1, v0, v1, st, spin_ns);
+        int c[TRSV_EPL];
+        T v[TRSV_EPL];
+#pragma unroll
+        for (int k = 0; k < TRSV_EPL; k++) {
+          c[k] = active ? cur.c[k] : -1;
+          v[k] = T(0);
+          if (c[k] >= 0) v[k] = trsv_peek(x, stage, b0, b1, c[k]);
+        }
+        trsv_wait<TRSV_EPL, T>(x, stage, b0, b1, c, v, st, spin_ns);
         T acc = T(0);
-        if (c0 >= 0) acc = cur.a0 * v0;
-        if (c1 >= 0) acc += cur.a1 * v1;
-        // entries beyond the first two per lane (rows longer than 16); the
-        // trip count (wd - 16) / 8 is the same for every lane
+#pragma unroll
+        for (int k = 0; k < TRSV_EPL; k++)
+          if (c[k] >= 0) acc += cur.a[k] * v[k];
+        // entries beyond the first 16 of a row; the trip count
+        // (wd - 16) / TRSV_LANES is the same for every lane
         const int64_t e = base + (r - b0) * wd;
-        for (int k = g + 16; k < wd; k += 8) {
-          const int c = active ? __ldg(M.col + e + k) : -1;
-          T v = T(0), none = T(0);
-          if (c >= 0) v = trsv_peek(x, stage, b0, b1, c);
-          trsv_wait(x, stage, b0, b1, c, -1, v, none, st, spin_ns);
-          if (c >= 0) acc += __ldg(M.val + e + k) * v;
+        for (int k = g + 16; k < wd; k += TRSV_LANES) {
+          int ce[1] = {active ? __ldg(M.col + e + k) : -1};
+          T ve[1] = {T(0)};
+          if (ce[0] >= 0) ve[0] = trsv_peek(x, stage, b0, b1, ce[0]);
+          trsv_wait<1, T>(x, stage, b0, b1, ce, ve, st, spin_ns);
+          if (ce[0] >= 0) acc += __ldg(M.val + e + k) * ve[0];
         }
 #pragma unroll
-        for (int o = 4; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        for (int o = TRSV_LANES / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
         if (active && g == 0) {
-          const T v = (cur.rhs - acc) * cur.rdg;
-          stage[r - b0] = v;
-          st_relaxed(x + r, v);
+          const T val = (cur.rhs - acc) * cur.rdg;
+          stage[r - b0] = val;
+          st_relaxed(x + r, val);
         }
         if (rounds > 1) __syncwarp();
       }

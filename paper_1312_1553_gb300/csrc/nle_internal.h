@@ -1,21 +1,23 @@
 // Internal data structures of the nle library (host setup + CUDA kernels).
 //
 // Layout in HBM
-//   Every device vector and matrix is stored in the LEVEL ORDER of the IC
-//   factor L: position i holds original row perm[i], where perm lists the
-//   rows level by level (ascending row inside a level).  Relabelling the
+//   Every device vector and matrix is stored in SLAB-MAJOR, LEVEL-MINOR
+//   order: the rows are cut into one slab per CTA (bsize consecutive rows of
+//   the caller's order) and sorted by their level in the IC factor L inside
+//   each slab; position i holds the caller's row perm[i].  Relabelling the
 //   unknowns changes no arithmetic of the method (dot products are
-//   permutation invariant and P L P^T is still triangular because a row only
-//   depends on rows of lower level), but it makes every level a contiguous
-//   range, so the triangular solves read and write vectors with unit stride.
-//   Vectors are padded to npad (a multiple of the slice height) with zeros.
+//   permutation invariant and P L P^T stays triangular because a row only
+//   depends on rows of lower level), but every CTA then solves a contiguous
+//   range of rows.  Vectors are padded to npad (a multiple of the slice
+//   height) with zeros.
 //
-//   Sparse matrices use a sliced-ELL format ("SELL") with slice height
-//   H = 32 * VW rows, where VW = 16 / sizeof(T) consecutive rows belong to one
-//   thread: a warp owns one slice, a lane owns VW adjacent rows and loads
-//   their e-th entries with one 16-byte load (val[base + e*H + lane*VW + v]).
-//   Padding entries carry value 0 and column = the row itself (SpMV) or the
-//   always-ready slot npad (triangular solves).
+//   A uses a sliced-ELL format ("SELL") with slice height H = 32 * VW rows,
+//   where VW = 16 / sizeof(T) consecutive rows belong to one thread: a warp
+//   owns one slice, a lane owns VW adjacent rows and loads their e-th entries
+//   with one 16-byte load (val[base + e*H + lane*VW + v]); padding entries
+//   carry value 0 and column = the row itself.  The strictly triangular
+//   parts of L and L^T are stored per slab in ELL form (entries of a row
+//   contiguous, column -1 for padding).
 #pragma once
 #include <cstdint>
 
@@ -26,6 +28,15 @@ constexpr int NWARP = TPB / 32;  // warps per CTA
 constexpr int KMAX = 10;         // largest k_max
 constexpr int MMAX = 64;         // largest p (columns of Q)
 constexpr int RED_MAX = 160;     // reduction slots per pass
+// triangular solves: rows a warp takes at a time (4 or 8); lanes per row;
+// entries per lane fetched ahead (16 per row)
+#ifndef NLE_TRSV_ROWS
+#define NLE_TRSV_ROWS 4
+#endif
+constexpr int TRSV_ROWS = NLE_TRSV_ROWS;
+constexpr int TRSV_LANES = 32 / TRSV_ROWS;
+constexpr int TRSV_EPL = 16 / TRSV_LANES;
+static_assert(TRSV_ROWS == 4 || TRSV_ROWS == 8, "4 or 8 rows per warp");
 
 template <typename T>
 struct Sell {
@@ -97,12 +108,12 @@ struct Dev {
   int64_t npad = 0;     // padded size (multiple of 32*VW)
   int64_t nchunks = 0;  // npad / VW
   int ldq = 0;          // allocated columns of Q / Qt
-  int64_t bsize = 0;    // rows per CTA slab in the triangular solves (multiple of 4)
+  int64_t bsize = 0;    // rows per CTA slab in the triangular solves (multiple of TRSV_ROWS)
   Sell<T> A;            // A in working precision
   Sell<double> A64;     // A in FP64 (same pattern and layout as A)
   // strictly lower part of L and strictly upper part of U = L^T in the
   // slab-major order, ELL per slab (offset and width per slab, col -1 =
-  // padding), diagonal separate, and the round of every row in its group of 4
+  // padding), diagonal separate, and the round of every row in its group of TRSV_ROWS rows
   const int64_t *Loff = nullptr, *Uoff = nullptr;
   const int32_t *Lw = nullptr, *Uw = nullptr, *Lcol = nullptr, *Ucol = nullptr;
   const T *Lval = nullptr, *Uval = nullptr;

@@ -12,6 +12,8 @@
 // (so column j finds every k with L(j,k) != 0 without scanning).
 #include "nle_setup.h"
 
+#include "nle_internal.h"
+
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -337,7 +339,7 @@ static void pack(int64_t n, int64_t npad, int H, const std::vector<int64_t> &rp,
 }
 
 // Per-slab ELL of a strictly triangular matrix given by rows (relabelled
-// order), plus the round of every row inside its group of 4 rows: the length
+// order), plus the round of every row inside its group of TRSV_ROWS rows: the length
 // of the longest dependency chain ending at the row within the group
 // (lower: earlier rows of the group; upper: later rows).
 template <typename TV>
@@ -366,8 +368,8 @@ static void ell(int64_t n, int64_t npad, int64_t bsize, bool lower, const std::v
       }
     }
   out.round.assign(npad, 0);
-  for (int64_t g0 = 0; g0 < n; g0 += 4) {
-    const int64_t g1 = std::min(n, g0 + 4);
+  for (int64_t g0 = 0; g0 < n; g0 += TRSV_ROWS) {
+    const int64_t g1 = std::min(n, g0 + TRSV_ROWS);
     if (lev) {
       // one level per round: rank of the row's level among the group's
       // levels, ascending for L, descending for L^T

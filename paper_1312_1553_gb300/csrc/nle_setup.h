@@ -44,7 +44,7 @@ struct EllHost {
   std::vector<int32_t> width;  // per slab: entries per row, multiple of 8
   std::vector<int32_t> col;    // -1 = padding
   std::vector<TV> val;
-  std::vector<uint8_t> round;  // per row: its round inside its group of 4
+  std::vector<uint8_t> round;  // per row: its round inside its group of TRSV_ROWS rows
 };
 
 template <typename TV>
@@ -79,7 +79,7 @@ void slab_level_order(const Factor &F, int64_t bsize, const int32_t *locality, s
 void permute(int64_t n, const int64_t *rp, const int32_t *ci, const double *va, const Factor &F,
              const std::vector<int32_t> &perm, const std::vector<int32_t> &iperm, int64_t npad, Permuted &P);
 
-// level_rounds: split every group of 4 rows into one round per level (needed
+// level_rounds: split every group of TRSV_ROWS rows into one round per level (needed
 // when dependencies can point to later slabs; see trsv_block).
 template <typename TV>
 void build_sell(const Permuted &P, int H, int64_t bsize, bool level_rounds, SellSet<TV> &S);
