@@ -269,7 +269,7 @@ static Dev<T> make_dev(nle_t h) {
   D.Ucol = h->U_col.as<int32_t>();
   D.Uval = h->U_val.as<T>();
   D.Uround = h->U_round.as<uint8_t>();
-  D.diag = h->d_diag.as<T>();
+  D.rdiag = h->d_diag.as<T>();
   const int64_t np = h->npad, ext = h->npad + 32 * h->vw;
   T *v = h->vecs.as<T>();
   D.p = v + 0 * np;
@@ -321,8 +321,8 @@ template <typename T>
 static nle_status launch(nle_t h, int id, void **args) {
   void *fn = kernel_ptr<T>(id, h->rpc);
   if (!fn) return fail(h, NLE_ERR_ARG, "no kernel instance for this size");
-  // dynamic shared memory: the CTA's slab of the triangular solves
-  const size_t dyn = (size_t)h->bsize * (mixed(h) ? 4 : 8);
+  // dynamic shared memory: two slab-sized buffers of the triangular solves
+  const size_t dyn = 2 * (size_t)h->bsize * (mixed(h) ? 4 : 8);
   NLE_CUDA(h, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
   int nb = 0;
   NLE_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, TPB, dyn));
@@ -543,7 +543,7 @@ nle_status nle_factor_ic(nle_t h, int lfil, double tau_ic) {
   // one slab of rows per CTA in the triangular solves (a multiple of TRSV_ROWS rows,
   // staged in shared memory)
   h->bsize = ((h->npad + TRSV_ROWS * grid - 1) / (TRSV_ROWS * grid)) * TRSV_ROWS;
-  if (h->bsize * (int64_t)(mixed(h) ? 4 : 8) > 160 * 1024)
+  if (2 * h->bsize * (int64_t)(mixed(h) ? 4 : 8) > 192 * 1024)
     return fail(h, NLE_ERR_ARG, "n too large for the shared-memory slab of one persistent grid");
   // with a multicolour ordering the slabs still follow the caller's row
   // order (P0[k] = caller's row of row k of P A P^T), which keeps each
@@ -962,7 +962,7 @@ static nle_status batch_impl(int count, nle_t *hs, int p, double tol, int max_ne
     NLE_CUDA(h0, cudaMemsetAsync(h->state.p, 0, sizeof(State), h->stream));
     NLE_CUDA(h0, cudaStreamSynchronize(h->stream));
     while ((int64_t)rpc * h->grid * TPB < h->nchunks) rpc *= 2;
-    dyn = std::max(dyn, (size_t)h->bsize * sizeof(T));
+    dyn = std::max(dyn, 2 * (size_t)h->bsize * sizeof(T));
     order[b] = b;
   }
   if (rpc > 8) return fail(h0, NLE_ERR_ARG, "a problem is too large for its CTA group");

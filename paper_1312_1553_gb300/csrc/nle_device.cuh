@@ -330,8 +330,9 @@ __device__ __forceinline__ void sell_rows(const Sell<TV> &M, const TX *__restric
 // index without a dependent load.  A warp takes TRSV_ROWS consecutive rows
 // at a time, 32 / TRSV_ROWS lanes per row, 16 entries of each row in flight,
 // and fetches the
-// next group's entries, right-hand sides and pivots (as reciprocals, so no
-// division sits on the dependency chain) before the current group waits.
+// next group's entries, right-hand sides (from shared memory) and pivots
+// (reciprocals computed on the host, so no division and no load sits on the
+// dependency chain) before the current group waits.
 // The wait is warp-uniform: the warp re-polls the entries still missing
 // until every lane holds its values (a vote), then reduces with shuffles; a
 // per-lane wait followed by the warp's reconvergence measured about 1.5x
@@ -351,7 +352,7 @@ struct TriEll {
   const int32_t *width;  // per slab: entries per row (multiple of 8)
   const int32_t *col;    // -1 = padding
   const T *val;
-  const T *diag;          // npad
+  const T *rdiag;         // npad: reciprocal pivots 1 / L_rr
   const uint8_t *round;   // npad: round of the row inside its group of TRSV_ROWS rows
 };
 
@@ -383,7 +384,7 @@ __device__ __forceinline__ void trsv_fetch(const TriEll<T> &M, int64_t b0, int64
   P.rdg = T(1);
   if (g == 0) {
     P.rhs = rhs_of(r);
-    P.rdg = T(1) / __ldg(M.diag + r);
+    P.rdg = __ldg(M.rdiag + r);
   }
 }
 
@@ -447,14 +448,10 @@ __device__ __forceinline__ void trsv_block(const TriEll<T> &M, T *x, int64_t npa
     const int q = lane / TRSV_LANES, g = lane % TRSV_LANES;
     const int64_t base = __ldg(M.off + grank());
     const int wd = __ldg(M.width + grank());
-    TriPre<T> cur, nxt;
-    trsv_fetch<LOWER, T>(M, b0, base, wd, ngrp, it, q, g, rhs_of, cur);
-    for (;;) {
-      const int64_t itn = it + twarps;
-      const bool more = itn < ngrp;
-      // the next group's entries and right-hand sides load while this one waits
-      if (more) trsv_fetch<LOWER, T>(M, b0, base, wd, ngrp, itn, q, g, rhs_of, nxt);
-      const int64_t gi = LOWER ? it : ngrp - 1 - it;
+    // one group: its rounds, each a warp-uniform wait, the reduction and the
+    // publication of the round's rows
+    auto process = [&](const TriPre<T> &cur, int64_t itc) {
+      const int64_t gi = LOWER ? itc : ngrp - 1 - itc;
       const int64_t r = b0 + TRSV_ROWS * gi + q;
       const int rounds = 1 + __reduce_max_sync(0xffffffffu, (unsigned)cur.rnd);
       for (int rd = 0; rd < rounds; rd++) {
@@ -491,9 +488,21 @@ __device__ __forceinline__ void trsv_block(const TriEll<T> &M, T *x, int64_t npa
         }
         if (rounds > 1) __syncwarp();
       }
-      if (!more) break;
-      it = itn;
-      cur = nxt;
+    };
+    // two descriptor sets used in turn: the next group's entries load while
+    // this one waits, and no register copy waits for those loads
+    TriPre<T> p0, p1;
+    trsv_fetch<LOWER, T>(M, b0, base, wd, ngrp, it, q, g, rhs_of, p0);
+    for (;;) {
+      const int64_t it1 = it + twarps;
+      if (it1 < ngrp) trsv_fetch<LOWER, T>(M, b0, base, wd, ngrp, it1, q, g, rhs_of, p1);
+      process(p0, it);
+      if (it1 >= ngrp) break;
+      const int64_t it2 = it1 + twarps;
+      if (it2 < ngrp) trsv_fetch<LOWER, T>(M, b0, base, wd, ngrp, it2, q, g, rhs_of, p0);
+      process(p1, it1);
+      if (it2 >= ngrp) break;
+      it = it2;
     }
   }
   __syncthreads();

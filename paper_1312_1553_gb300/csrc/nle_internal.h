@@ -117,7 +117,7 @@ struct Dev {
   const int64_t *Loff = nullptr, *Uoff = nullptr;
   const int32_t *Lw = nullptr, *Uw = nullptr, *Lcol = nullptr, *Ucol = nullptr;
   const T *Lval = nullptr, *Uval = nullptr;
-  const T *diag = nullptr;  // diagonal of L (1 on padding rows)
+  const T *rdiag = nullptr;  // reciprocal diagonal of L (1 on padding rows)
   const uint8_t *Lround = nullptr, *Uround = nullptr;
   // working-precision vectors (npad; z and c0 have npad + 32*VW entries)
   T *p, *y, *s, *g, *z, *c0, *rT, *x, *Ax, *Ap;

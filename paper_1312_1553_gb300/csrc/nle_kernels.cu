@@ -212,30 +212,43 @@ __device__ bool gram(const Dev<T> &D, Shared &sh, Ctl &ctl, int m, int k) {
 // queues are reset.  *gamma_new receives gamma' = g^T c.
 //
 // The triangular solves (trsv_block) work slab by slab, one slab per CTA,
-// with ctl.twarps warps of the CTA taking the slab's row pairs in order.
+// with ctl.twarps warps of the CTA taking the slab's rows in order.  Dynamic
+// shared memory holds two slab-sized buffers: A receives the forward results
+// z of the slab, B first holds the forward right-hand side w and then the
+// backward results; no right-hand side is fetched from global memory on the
+// dependency chain.
 // ---------------------------------------------------------------------------
-extern __shared__ __align__(16) unsigned char nle_dyn_smem[];  // slab of the triangular solves
+extern __shared__ __align__(16) unsigned char nle_dyn_smem[];  // two slabs of the triangular solves
 
 template <typename T>
 __device__ __forceinline__ void trsv_forward(const Dev<T> &D, Shared &sh, const Ctl &ctl, int k) {
-  const TriEll<T> L{D.Loff, D.Lw, D.Lcol, D.Lval, D.diag, D.Lround};
-  trsv_block<true, T>(L, D.z, D.npad, D.bsize, ctl.twarps, ctl.spin_ns, D.st,
-                      reinterpret_cast<T *>(nle_dyn_smem), [&](int64_t r) {
-                        T w = __ldcg(D.g + r);
-                        for (int t = 0; t < k; t++)
-                          w -= T(sh.a[t]) * __ldcg(D.R + (int64_t)sh.order[t] * D.npad + r);
-                        return w;
-                      });
+  const TriEll<T> L{D.Loff, D.Lw, D.Lcol, D.Lval, D.rdiag, D.Lround};
+  T *bufA = reinterpret_cast<T *>(nle_dyn_smem);
+  T *bufB = bufA + D.bsize;
+  const int64_t b0 = (int64_t)grank() * D.bsize;
+  const int64_t nb = max((int64_t)0, min(D.npad, b0 + D.bsize) - b0);
+  // w = g - R a for the slab's rows (trsv_block's first barrier orders these
+  // stores before any use)
+  for (int64_t i = threadIdx.x; i < nb; i += blockDim.x) {
+    T w = __ldcg(D.g + b0 + i);
+    for (int t = 0; t < k; t++) w -= T(sh.a[t]) * __ldcg(D.R + (int64_t)sh.order[t] * D.npad + b0 + i);
+    bufB[i] = w;
+  }
+  trsv_block<true, T>(L, D.z, D.npad, D.bsize, ctl.twarps, ctl.spin_ns, D.st, bufA,
+                      [&](int64_t r) { return bufB[r - b0]; });
 }
 
 // The right-hand side of the backward solve is the forward result of the
-// CTA's own slab, complete after trsv_forward's closing __syncthreads, so no
-// grid barrier separates the two solves.
+// CTA's own slab (buffer A), complete after trsv_forward's closing
+// __syncthreads, so no grid barrier separates the two solves.
 template <typename T>
 __device__ __forceinline__ void trsv_backward(const Dev<T> &D, const Ctl &ctl) {
-  const TriEll<T> U{D.Uoff, D.Uw, D.Ucol, D.Uval, D.diag, D.Uround};
-  trsv_block<false, T>(U, D.c0, D.npad, D.bsize, ctl.twarps, ctl.spin_ns, D.st,
-                       reinterpret_cast<T *>(nle_dyn_smem), [&](int64_t r) { return __ldcg(D.z + r); });
+  const TriEll<T> U{D.Uoff, D.Uw, D.Ucol, D.Uval, D.rdiag, D.Uround};
+  const T *bufA = reinterpret_cast<const T *>(nle_dyn_smem);
+  T *bufB = reinterpret_cast<T *>(nle_dyn_smem) + D.bsize;
+  const int64_t b0 = (int64_t)grank() * D.bsize;
+  trsv_block<false, T>(U, D.c0, D.npad, D.bsize, ctl.twarps, ctl.spin_ns, D.st, bufB,
+                       [&](int64_t r) { return bufA[r - b0]; });
 }
 
 template <typename T>

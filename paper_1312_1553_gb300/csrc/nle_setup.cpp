@@ -403,7 +403,7 @@ void build_sell(const Permuted &P, int H, int64_t bsize, bool level_rounds, Sell
   ell<TV>(P.n, P.npad, bsize, true, P.Lrp, P.Lcol, P.Lval, lev, S.L);
   ell<TV>(P.n, P.npad, bsize, false, P.Urp, P.Ucol, P.Uval, lev, S.U);
   S.diag.assign(P.npad, TV(1));
-  for (int64_t i = 0; i < P.n; i++) S.diag[i] = TV(P.diag[i]);
+  for (int64_t i = 0; i < P.n; i++) S.diag[i] = TV(1.0 / P.diag[i]);  // reciprocal pivots
 }
 
 template void build_sell<float>(const Permuted &, int, int64_t, bool, SellSet<float> &);

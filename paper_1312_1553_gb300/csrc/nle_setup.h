@@ -52,7 +52,7 @@ struct SellSet {
   SellHost<TV> A;
   SellHost<double> A64;
   EllHost<TV> L, U;      // strictly lower / upper parts, slab-major order
-  std::vector<TV> diag;  // npad, 1 on padding rows
+  std::vector<TV> diag;  // npad: reciprocal pivots 1 / L_ii, 1 on padding rows
 };
 
 // 0 on success; 2 = malformed CSR, 3 = non-positive diagonal (msg says why).
