@@ -238,11 +238,18 @@ def alg_bytes(n, nnz_a, nnz_l, w, its, sum_m, sum_k, kind):
 
 
 def kernel_hash() -> str:
+    """Hash of the library's code with comments and blank space removed, so
+    that a captured traffic figure stays valid across comment-only edits."""
+    import re
+
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_1312_1553_gb300", "csrc")
     for f in sorted(os.listdir(d)):
-        with open(os.path.join(d, f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(d, f), encoding="utf-8") as fh:
+            code = fh.read()
+        code = re.sub(r"/\*.*?\*/", " ", code, flags=re.S)
+        code = re.sub(r"//[^\n]*", " ", code)
+        h.update(f.encode() + b"\0" + " ".join(code.split()).encode())
     return h.hexdigest()[:16]
 
 

@@ -181,9 +181,11 @@ nle_status nle_create(int64_t n, int64_t nnz, const int64_t *rowptr, const int32
  * w[j] must be positive; L(j,j) = sqrt(w[j]), L(i,j) = w[i]/L(j,j); an
  * off-diagonal is dropped when |L(i,j)| < tau_IC ||A(:,j)||_2; of the rest
  * the lfil largest in modulus are kept (ties to the smaller row).
- * The factor and its levels are uploaded once; the device then works in
- * the level order of L (a relabelling of the unknowns; the method is
- * unchanged).  Errors: NLE_ERR_ARG (lfil < 0, tau_IC < 0),
+ * The factor and its levels are uploaded once; the device then works in a
+ * slab-major, level-minor order of the unknowns (one slab of consecutive
+ * rows per CTA, sorted by level of L inside the slab: a relabelling, the
+ * method is unchanged).  With nle_options.ordering the factor is that of
+ * P A P^T for the multicolour permutation P.  Errors: NLE_ERR_ARG (lfil < 0, tau_IC < 0),
  * NLE_ERR_NOT_SPD (non-positive pivot), NLE_ERR_OOM, NLE_ERR_CUDA.
  * Calling it again refactors with the new parameters. */
 nle_status nle_factor_ic(nle_t h, int lfil, double tau_ic);

@@ -94,7 +94,7 @@ __global__ void k_output_vectors(double *V, const double *Qt, const int32_t *ipe
   if (threadIdx.x == 0) st->sign[j] = sgn;
   for (int64_t o = threadIdx.x; o < n; o += blockDim.x) V[(int64_t)j * n + o] = sgn * q[iperm[o]];
 }
-// dst[i] = sign_j * src[perm[i]] (FP64, level order), 0 on padding
+// dst[i] = sign_j * src[perm[i]] (FP64, device order), 0 on padding
 __global__ void k_gather_signed(double *dst, const double *src, const int32_t *perm, int64_t n, int64_t npad,
                                 const State *st, int j) {
   const double sg = st->sign[j];
@@ -190,7 +190,7 @@ struct nle_ctx {
   DBuf part, state;
   DBuf scratch;  // 2 * n doubles for host transfers
   DBuf d_erow, d_ecol, d_grad;  // natural-order entries (adjoint)
-  DBuf dX0;                      // start vectors for the batched kernel (p columns, level order)
+  DBuf dX0;                      // start vectors for the batched kernel (p columns, device order)
   std::vector<double> pinned_dummy;
   bool solved = false;
   int last_p = 0;
@@ -360,7 +360,7 @@ static nle_status ensure_q(nle_t h, int m) {
 }
 
 // Copy p vectors of length n (natural order, FP64, host or device) into a
-// device array of working-precision columns (level order) at dst + c*npad.
+// device array of working-precision columns (device order) at dst + c*npad.
 template <typename T>
 static nle_status put_vectors(nle_t h, const double *src, int count, T *dst, int on_device) {
   const int64_t n = h->n;

@@ -121,7 +121,7 @@ struct Dev {
   const uint8_t *Lround = nullptr, *Uround = nullptr;
   // working-precision vectors (npad; z and c0 have npad + 32*VW entries)
   T *p, *y, *s, *g, *z, *c0, *rT, *x, *Ax, *Ap;
-  const T *X0 = nullptr;  // optional: start vectors (p columns, level order) for the whole-solve kernel
+  const T *X0 = nullptr;  // optional: start vectors (p columns, device order) for the whole-solve kernel
   int grid = 0;           // CTAs this problem's layout was built for (slabs)
   T *Q;        // npad * ldq, column c at Q + c*npad (converged v_1.. and u)
   T *S, *R;    // npad * KMAX, BFGS pairs by physical slot

@@ -1165,7 +1165,7 @@ __global__ void __launch_bounds__(TPB, 1) k_pcg(Dev<T> D, Opts O, int m, int k, 
 
 // ---------------------------------------------------------------------------
 // Kernel: adjoint solve for eigenvector j (not in the paper).
-// On entry b64 holds gbar_j (level order, FP64, already multiplied by the
+// On entry b64 holds gbar_j (device order, FP64, already multiplied by the
 // sign of the output eigenvector); Qt holds v_1..v_p (FP64) and Q their
 // working-precision shadows; st->lambda the eigenvalues.  Computes
 //   c_i = v_i^T gbar,   b = gbar - V c,

@@ -1,6 +1,7 @@
 // Host-side set-up of the nle library: CSR validation, the IC(lfil, tau_IC)
-// factor (Section 2), the level sets of L and L^T, the level-order
-// relabelling and the packing of the sliced-ELL matrices.
+// factor (Section 2), the level sets of L and L^T, the optional multicolour
+// ordering, the slab-major level-minor relabelling and the packing of the
+// sliced-ELL and per-slab ELL matrices.
 //
 // The factor is the preconditioner Phat_0 = (L L^T)^{-1} of Section 2.  The
 // paper does not print the IC variant; the library uses a left-looking column

@@ -20,7 +20,7 @@ struct Factor {
   int64_t nlevL = 0, nlevU = 0;
 };
 
-// Relabelled (level-order) matrices, row by row.
+// Relabelled (slab-major, level-minor) matrices, row by row.
 struct Permuted {
   int64_t n = 0, npad = 0;
   std::vector<int64_t> Arp, Lrp, Urp;
