@@ -12,8 +12,9 @@
  *     Q = [v_1 .. v_{j-1} u_k] (Section 4.3);
  *   - the PCG preconditioner P_k = (I-QQ^T) Phat_k (I-QQ^T), with Phat_0 =
  *     (L L^T)^{-1}, L = IC(lfil, tau_IC, A) (Section 2), updated by the
- *     simplified BFGS formula eq. "lastprec" and applied by Algorithm 3.1
- *     with at most k_max stored pairs (Section 4.4);
+ *     simplified BFGS formula eq. "lastprec" (or, as an option, the full
+ *     formula of Section 3) and applied by Algorithm 3.1 with at most k_max
+ *     stored pairs (Section 4.4);
  *   - the initial guess of each eigenpair from DACG (Section 4.1);
  *   - driven by Algorithm 3.2.
  * The sign convention of the paper is r = A u - theta u, J_k s = -r, so the
