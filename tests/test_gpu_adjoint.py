@@ -52,6 +52,35 @@ def test_backward_matches_oracle_adjoint(nle, prec):
 
 
 @pytest.mark.parametrize("prec", PRECS)
+def test_backward_with_multicolour_ordering(nle, prec):
+    """The gradient does not depend on the preconditioner: with the
+    distance-2 multicolour ordering (factor of P A P^T, device order through
+    P) nle_backward still returns dL/dA per stored entry of A in the
+    caller's numbering, equal to the oracle's adjoint on A itself."""
+    A, st = W.workload("diff2d5_60x70")
+    p = st["p"]
+    X0 = W.start_vectors(A.n, p, st["seed"])
+    s = nle.Eigensolver(A, dict(precision=nle.NLE_MIXED if prec == "mixed" else nle.NLE_FP64,
+                                ordering=nle.NLE_ORDER_MULTICOLOR2))
+    s.factor_ic(st["lfil"], st["tau_ic"])
+    lam, V, stats = s.solve(p, 1e-10, 100, 20, X0)
+    V = V.cpu().numpy()
+    w = A.meta["w"]
+    gl = np.ones(p)
+    gV = np.zeros((p, A.n))
+    gV[0] = 2 * w * V[0]
+    grad = s.backward(gl, gV).cpu().numpy()
+    s.close()
+    ic = O.ic_factor(A, st["lfil"], st["tau_ic"])
+    lref, Vref, _ = O.dacg_newton(A, p, X0, O.OracleOptions(tol=1e-10, lfil=st["lfil"], tau_ic=st["tau_ic"]), ic=ic)
+    gVref = np.zeros((A.n, p))
+    gVref[:, 0] = 2 * w * Vref[:, 0]
+    ref = O.adjoint_grad(A, lref, Vref, gl, gVref, ic)
+    err = np.linalg.norm(grad - ref) / np.linalg.norm(ref)
+    assert err <= 1e-6, err
+
+
+@pytest.mark.parametrize("prec", PRECS)
 def test_backward_eigenvalue_closed_form(nle, prec):
     """d lambda_{k,l}/d a = 2 - 2 cos(k pi/(nx+1)) for the anisotropic Laplacian (a = 1, b = 1.7)."""
     nx, ny = 30, 37
