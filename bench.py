@@ -267,6 +267,25 @@ def load_traffic(kernel: str):
     return e.get("bytes_per_launch")
 
 
+def max_over_ranks(values, device="cuda"):
+    """Element-wise maximum of per-rank timings (seconds) over all ranks of
+    the default process group; the values themselves when there is none.
+    Replicas run independently, so the job's time is the slowest rank's."""
+    import torch
+
+    if not (torch.distributed.is_available() and torch.distributed.is_initialized()):
+        return [float(v) for v in values]
+    tt = torch.tensor([float(v) for v in values], device=device, dtype=torch.float64)
+    torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+    return [float(v) for v in tt]
+
+
+def replica_throughput(world: int, units_per_rank_step: int, steps: int, t_max: float) -> float:
+    """Whole-job throughput of `world` independent replicas (weak scaling):
+    all units processed by all ranks over the slowest rank's time."""
+    return world * units_per_rank_step * steps / t_max
+
+
 def peak_hbm():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -360,11 +379,7 @@ def batch_main(args, world, rank, local, cpu):
         e2e_sec = max(time.perf_counter() - t0, 1e-9)
         for s in solvers:
             s.close()
-    t_max, e2e_max = ms / 1000.0, e2e_sec
-    if world > 1:
-        tt = torch.tensor([t_max, e2e_max], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_max, e2e_max = float(tt[0]), float(tt[1])
+    t_max, e2e_max = max_over_ranks([ms / 1000.0, e2e_sec])
     if args.skip_e2e:
         e2e_max = float("inf")
     pairs = count * BATCH_P
@@ -376,7 +391,7 @@ def batch_main(args, world, rank, local, cpu):
     peak, peak_kind = peak_hbm()
     achieved = (b_step / 1e9) / (ms_launch / 1e3)
     line = dict(metric=f"eigenpairs/s, {count} graph Laplacians batched, rel. residual 1e-8",
-                value=world * pairs * args.steps / t_max, unit=UNIT, n_gpus=world, steps=args.steps,
+                value=replica_throughput(world, pairs, args.steps, t_max), unit=UNIT, n_gpus=world, steps=args.steps,
                 warmup=args.warmup, ms_per_step=1000 * t_max / args.steps, higher_is_better=True, scaling="weak",
                 vs_baseline=None, dtype="f32" if prec == nle.NLE_MIXED else "f64", data="synthetic",
                 config=dict(workload=f"{BATCH}: {count} random geometric graph Laplacians + 1e-3 I, "
@@ -390,7 +405,7 @@ def batch_main(args, world, rank, local, cpu):
                               else "fallback 6.8 TB/s", alg_bytes_per_launch=b_step, ms_per_launch=ms_launch),
                 cpu_baseline=cpu,
                 e2e=None if args.skip_e2e else dict(
-                    value=world * pairs * args.steps / e2e_max, unit=UNIT,
+                    value=replica_throughput(world, pairs, args.steps, e2e_max), unit=UNIT,
                     h2d_bytes_per_step=sum(x.numel() * 8 for x in X0h), d2h_bytes_per_step=count * BATCH_P * 8),
                 clocks=clocks, gpu_launches=args.steps * (1 + count * (BATCH_P + 1)),
                 iterations=dict(pcg=sum(st["pcg_iterations"] for st in stats),
@@ -518,16 +533,11 @@ def main():
         s.close()
 
     # max over ranks
-    t_max = ms / 1000.0
-    e2e_max = e2e_sec
-    if world > 1:
-        tt = torch.tensor([t_max, e2e_max], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_max, e2e_max = float(tt[0]), float(tt[1])
+    t_max, e2e_max = max_over_ranks([ms / 1000.0, e2e_sec])
     if args.skip_e2e:
         e2e_max = float("inf")
-    value = world * p * args.steps / t_max
-    e2e_value = world * p * args.steps / e2e_max
+    value = replica_throughput(world, p, args.steps, t_max)
+    e2e_value = replica_throughput(world, p, args.steps, e2e_max)
 
     # roofline of the dominant kernel (Newton phase or DACG phase)
     w = 4 if prec == nle.NLE_MIXED else 8
