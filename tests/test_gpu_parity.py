@@ -378,6 +378,29 @@ def test_solve_full_size_hex27_96(nle):
 # edge cases and failure reporting
 # ---------------------------------------------------------------------------
 
+def test_default_start_and_host_buffers(nle):
+    """X0 = NULL (the library's fixed pseudo-random starts) still finds the
+    closed-form leftmost eigenvalues; the same solve through host buffers
+    (buffers_on_device = 0) returns exactly the device-buffer results."""
+    A, st = load("aniso2d_30x37")
+    p = 3
+    exact = W.laplacian_2d_aniso_eigs(30, 37, 1.0, 1.7)[:p]
+    s = solver(nle, A, "fp64")
+    s.factor_ic(st["lfil"], st["tau_ic"])
+    lam, V, stats = s.solve(p, 1e-10, 100, 20, None)
+    np.testing.assert_allclose(lam.cpu().numpy(), exact, rtol=1e-10)
+    X0 = np.ascontiguousarray(W.start_vectors(A.n, p, st["seed"]))
+    lam_d, V_d, _ = s.solve(p, 1e-10, 100, 20, X0)
+    lam_h = np.zeros(p)
+    V_h = np.zeros((p, A.n))
+    stats_h = nle.nle_stats()
+    rc = nle.nle_solve(s.h, p, 1e-10, 100, 20, nle._hptr(X0), nle._hptr(lam_h), nle._hptr(V_h), stats_h, 0)
+    assert rc == nle.NLE_OK, nle.nle_last_error(s.h)
+    np.testing.assert_array_equal(lam_h, lam_d.cpu().numpy())
+    np.testing.assert_array_equal(V_h, V_d.cpu().numpy())
+    s.close()
+
+
 def test_p1_and_tiny_problem(nle):
     A = W.tridiag(7, 2.0, -1.0)
     s = solver(nle, A, "fp64")
