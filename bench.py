@@ -253,8 +253,9 @@ def kernel_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def load_traffic(kernel: str):
-    """ncu dram bytes per launch of `kernel`, if captured for the current sources."""
+def load_traffic(kernel: str, workload: str):
+    """ncu dram bytes per launch of `kernel` on `workload` (the bench's
+    launch configuration), if captured for the current sources."""
     p = os.path.join(ROOT, "profiles", "traffic.txt")
     try:
         with open(p) as fh:
@@ -262,7 +263,7 @@ def load_traffic(kernel: str):
     except Exception:
         return None
     e = t.get(kernel)
-    if not e or e.get("kernel_hash") != kernel_hash():
+    if not e or e.get("kernel_hash") != kernel_hash() or e.get("workload") != workload:
         return None
     return e.get("bytes_per_launch")
 
@@ -400,7 +401,7 @@ def batch_main(args, world, rank, local, cpu):
                             tol=1e-8, ic_seconds=ic_seconds, l2="working set > 129 MB L2 (no flush needed)",
                             parallelism=f"replicas{world}" if world > 1 else f"single GPU, groups of {4 if prec == nle.NLE_MIXED else 8} CTAs"),
                 roofline=dict(bound="hbm", achieved=achieved, peak=peak, unit="GB/s", frac=achieved / peak,
-                              traffic=load_traffic("k_batch"), kernel="k_batch",
+                              traffic=load_traffic("k_batch", BATCH), kernel="k_batch",
                               peak_source=f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)" if peak_kind == "measured"
                               else "fallback 6.8 TB/s", alg_bytes_per_launch=b_step, ms_per_launch=ms_launch),
                 cpu_baseline=cpu,
@@ -554,7 +555,8 @@ def main():
     b, msk = (b_newton, ms_newton) if kern == "k_newton" else (b_dacg, ms_dacg)
     achieved = (b / 1e9) / (msk / 1e3)
     nlaunch = launches_per_step * args.steps
-    traffic = load_traffic(kern)
+    traffic = load_traffic(kern, args.workload) if not (args.ordering != "natural" or args.bfgs != "simplified" or
+                                                       prec != nle.NLE_MIXED or args.pairs) else None
     roof = dict(bound="hbm", achieved=achieved, peak=peak, unit="GB/s", frac=achieved / peak, traffic=traffic,
                 kernel=kern, peak_source=f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)" if peak_kind == "measured" else
                 "fallback 6.8 TB/s", alg_bytes_per_launch=b / nlaunch, ms_per_launch=msk / nlaunch,
