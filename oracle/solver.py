@@ -29,6 +29,10 @@ R-reorth  After u_{k+1} = (u_k+s_k)/||u_k+s_k|| the new iterate is
 R-dacg    DACG (cited, not printed) is read as preconditioned nonlinear CG
           on the Rayleigh quotient restricted to the complement of the
           converged eigenvectors, with an exact line search.
+R-full    The full BFGS update of Section 3 (option ``bfgs_full``) takes
+          y_k = r_{k+1} - r_k in the same sign convention; the stored pair
+          is (s_k, w_k = -y_k), which the simplified update (eq.
+          "lastprec", the default) replaces by (s_k, r_k).
 """
 from __future__ import annotations
 
