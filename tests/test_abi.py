@@ -132,3 +132,15 @@ def test_multicolor_order_argument_errors(lib):
     with pytest.raises(nle.NLEError) as e:
         nle.multicolor_order(bad, 1)
     assert e.value.args and "column" in str(e.value)
+
+
+def test_permute_is_symmetric_permutation():
+    """workloads.permute(A, perm) = P A P^T with row k = row perm[k] of A:
+    the dense matrices agree entry by entry and the columns stay sorted."""
+    A, _ = W.workload("aniso2d_30x37")
+    perm, _ = W.multicolor_order(A, 2)
+    B = W.permute(A, perm)
+    np.testing.assert_array_equal(B.dense(), A.dense()[np.ix_(perm, perm)])
+    for i in range(B.n):
+        c = B.col[B.rowptr[i]:B.rowptr[i + 1]]
+        assert np.all(np.diff(c) > 0)
