@@ -294,15 +294,18 @@ nle_status nle_multicolor_order(int64_t n, const int64_t *rowptr, const int32_t 
  * cudaMalloc's implicit device synchronisation and latency are not
  * acceptable, or programs that must finish all allocation at start-up.
  *
- * c = (L L^T)^{-1} g, the incomplete-Cholesky part P0hat of the
- * preconditioner (Section 2), in FP64, with L given by the caller:
+ * c = (L L^T)^{-1} g, the incomplete-Cholesky part of the preconditioner,
+ * in FP64, with L given by the caller:
  *   Lrp[n+1], Lcol, Lval: the strictly lower part of L in CSR (int32 row
  *     pointers), rows in natural order;
  *   Urp[n+1], Ucol, Uval: the strictly upper part of U = L^T in CSR;
- *   diag[n]: the diagonal of L;  g[n]: input;  c[n]: output.
+ *   diag[n]: the diagonal of L;  g[n]: input;  c[n]: output, which must
+ *     not overlap g (NLE_ERR_ARG otherwise: no in-place application).
  * Every pointer is a device pointer owned by the caller; stream is the
- * cudaStream_t the work is ordered on (NULL = legacy default stream); the
- * call returns after that work has completed.
+ * cudaStream_t the work is ordered on (NULL = legacy default stream).  The
+ * call reads its error word back on that stream and waits for the stream
+ * before it returns.  It clears the runtime's pending launch error (if an
+ * earlier launch of the caller left one) before its own launches.
  *
  * It allocates nothing: its only temporary storage is one fixed array of
  * NLE_NOALLOC_MAX_N + 32 doubles (about 2 MB) compiled into the library,
@@ -311,8 +314,8 @@ nle_status nle_multicolor_order(int64_t n, const int64_t *rowptr, const int32_t 
  *   - n must be 1..NLE_NOALLOC_MAX_N; larger n returns NLE_ERR_ARG with a
  *     message in nle_last_error(NULL) and touches no memory;
  *   - the first call on a device looks up the array's device address once
- *     for that device (cudaGetSymbolAddress, with that device current), so
- *     make that first call before any stream capture;
+ *     for that device (cudaGetSymbolAddress, with that device current);
+ *     make that first call before any stream capture begins;
  *   - all calls share the array and it keeps the last call's contents (the
  *     call resets what must start fresh), so calls that overlap on the GPU,
  *     on any streams or threads, race: serialise them;

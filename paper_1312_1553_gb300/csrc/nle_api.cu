@@ -226,22 +226,26 @@ static nle_status fail(nle_t h, nle_status code, const std::string &msg) {
     }                                                                                      \
   } while (0)
 
-static cudaError_t dalloc(DBuf &b, size_t bytes) {
+// Allocation, zeroing and uploads are ordered on the stream the kernels
+// run on (a non-blocking stream does not wait for the legacy default
+// stream).  A copy from pageable host memory returns once the data is
+// staged, so the host vector may be released right after the call.
+static cudaError_t dalloc(DBuf &b, size_t bytes, cudaStream_t stream) {
   b.reset();
   if (bytes == 0) bytes = 16;
   cudaError_t e = cudaMalloc(&b.p, bytes);
   if (e == cudaSuccess) {
     b.bytes = bytes;
-    e = cudaMemset(b.p, 0, bytes);
+    e = cudaMemsetAsync(b.p, 0, bytes, stream);
   }
   return e;
 }
 
 template <typename X>
-static cudaError_t upload(DBuf &b, const std::vector<X> &v) {
-  cudaError_t e = dalloc(b, v.size() * sizeof(X));
+static cudaError_t upload(DBuf &b, const std::vector<X> &v, cudaStream_t stream) {
+  cudaError_t e = dalloc(b, v.size() * sizeof(X), stream);
   if (e != cudaSuccess) return e;
-  if (!v.empty()) e = cudaMemcpy(b.p, v.data(), v.size() * sizeof(X), cudaMemcpyHostToDevice);
+  if (!v.empty()) e = cudaMemcpyAsync(b.p, v.data(), v.size() * sizeof(X), cudaMemcpyHostToDevice, stream);
   return e;
 }
 
@@ -353,8 +357,8 @@ static nle_status check_state_error(nle_t h) {
 static nle_status ensure_q(nle_t h, int m) {
   if (m <= h->ldq) return NLE_OK;
   const size_t tsz = mixed(h) ? 4 : 8;
-  NLE_CUDA(h, dalloc(h->dQ, (size_t)h->npad * m * tsz));
-  NLE_CUDA(h, dalloc(h->dQt, (size_t)h->npad * m * 8));
+  NLE_CUDA(h, dalloc(h->dQ, (size_t)h->npad * m * tsz, h->stream));
+  NLE_CUDA(h, dalloc(h->dQt, (size_t)h->npad * m * 8, h->stream));
   h->ldq = m;
   return NLE_OK;
 }
@@ -445,9 +449,12 @@ nle_status nle_create(int64_t n, int64_t nnz, const int64_t *rowptr, const int32
   h->col.resize(nnz);
   h->val.resize(nnz);
   if (on_device) {
-    if (cudaMemcpy(h->rowptr.data(), rowptr, (n + 1) * 8, cudaMemcpyDeviceToHost) != cudaSuccess ||
-        cudaMemcpy(h->col.data(), col, nnz * 4, cudaMemcpyDeviceToHost) != cudaSuccess ||
-        cudaMemcpy(h->val.data(), val, nnz * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
+    // read on the caller's stream, after the work that produced the arrays
+    cudaStream_t cs = (cudaStream_t)stream;
+    if (cudaMemcpyAsync(h->rowptr.data(), rowptr, (n + 1) * 8, cudaMemcpyDeviceToHost, cs) != cudaSuccess ||
+        cudaMemcpyAsync(h->col.data(), col, nnz * 4, cudaMemcpyDeviceToHost, cs) != cudaSuccess ||
+        cudaMemcpyAsync(h->val.data(), val, nnz * 8, cudaMemcpyDeviceToHost, cs) != cudaSuccess ||
+        cudaStreamSynchronize(cs) != cudaSuccess)
       return fail(nullptr, NLE_ERR_CUDA, "copy of the CSR arrays failed");
   } else {
     memcpy(h->rowptr.data(), rowptr, (n + 1) * 8);
@@ -560,53 +567,54 @@ nle_status nle_factor_ic(nle_t h, int lfil, double tau_ic) {
   if (mixed(h)) {
     SellSet<float> S;
     build_sell<float>(P, H, h->bsize, !P0.empty(), S);
-    NLE_CUDA(h, upload(h->A_sptr, S.A.sptr));
-    NLE_CUDA(h, upload(h->A_col, S.A.col));
-    NLE_CUDA(h, upload(h->A_val, S.A.val));
-    NLE_CUDA(h, upload(h->A64_val, S.A64.val));
-    NLE_CUDA(h, upload(h->L_off, S.L.off));
-    NLE_CUDA(h, upload(h->L_w, S.L.width));
-    NLE_CUDA(h, upload(h->L_col, S.L.col));
-    NLE_CUDA(h, upload(h->L_val, S.L.val));
-    NLE_CUDA(h, upload(h->L_round, S.L.round));
-    NLE_CUDA(h, upload(h->U_off, S.U.off));
-    NLE_CUDA(h, upload(h->U_w, S.U.width));
-    NLE_CUDA(h, upload(h->U_col, S.U.col));
-    NLE_CUDA(h, upload(h->U_val, S.U.val));
-    NLE_CUDA(h, upload(h->U_round, S.U.round));
-    NLE_CUDA(h, upload(h->d_diag, S.diag));
+    NLE_CUDA(h, upload(h->A_sptr, S.A.sptr, h->stream));
+    NLE_CUDA(h, upload(h->A_col, S.A.col, h->stream));
+    NLE_CUDA(h, upload(h->A_val, S.A.val, h->stream));
+    NLE_CUDA(h, upload(h->A64_val, S.A64.val, h->stream));
+    NLE_CUDA(h, upload(h->L_off, S.L.off, h->stream));
+    NLE_CUDA(h, upload(h->L_w, S.L.width, h->stream));
+    NLE_CUDA(h, upload(h->L_col, S.L.col, h->stream));
+    NLE_CUDA(h, upload(h->L_val, S.L.val, h->stream));
+    NLE_CUDA(h, upload(h->L_round, S.L.round, h->stream));
+    NLE_CUDA(h, upload(h->U_off, S.U.off, h->stream));
+    NLE_CUDA(h, upload(h->U_w, S.U.width, h->stream));
+    NLE_CUDA(h, upload(h->U_col, S.U.col, h->stream));
+    NLE_CUDA(h, upload(h->U_val, S.U.val, h->stream));
+    NLE_CUDA(h, upload(h->U_round, S.U.round, h->stream));
+    NLE_CUDA(h, upload(h->d_diag, S.diag, h->stream));
   } else {
     SellSet<double> S;
     build_sell<double>(P, H, h->bsize, !P0.empty(), S);
-    NLE_CUDA(h, upload(h->A_sptr, S.A.sptr));
-    NLE_CUDA(h, upload(h->A_col, S.A.col));
-    NLE_CUDA(h, upload(h->A_val, S.A.val));
-    NLE_CUDA(h, upload(h->A64_val, S.A64.val));
-    NLE_CUDA(h, upload(h->L_off, S.L.off));
-    NLE_CUDA(h, upload(h->L_w, S.L.width));
-    NLE_CUDA(h, upload(h->L_col, S.L.col));
-    NLE_CUDA(h, upload(h->L_val, S.L.val));
-    NLE_CUDA(h, upload(h->L_round, S.L.round));
-    NLE_CUDA(h, upload(h->U_off, S.U.off));
-    NLE_CUDA(h, upload(h->U_w, S.U.width));
-    NLE_CUDA(h, upload(h->U_col, S.U.col));
-    NLE_CUDA(h, upload(h->U_val, S.U.val));
-    NLE_CUDA(h, upload(h->U_round, S.U.round));
-    NLE_CUDA(h, upload(h->d_diag, S.diag));
+    NLE_CUDA(h, upload(h->A_sptr, S.A.sptr, h->stream));
+    NLE_CUDA(h, upload(h->A_col, S.A.col, h->stream));
+    NLE_CUDA(h, upload(h->A_val, S.A.val, h->stream));
+    NLE_CUDA(h, upload(h->A64_val, S.A64.val, h->stream));
+    NLE_CUDA(h, upload(h->L_off, S.L.off, h->stream));
+    NLE_CUDA(h, upload(h->L_w, S.L.width, h->stream));
+    NLE_CUDA(h, upload(h->L_col, S.L.col, h->stream));
+    NLE_CUDA(h, upload(h->L_val, S.L.val, h->stream));
+    NLE_CUDA(h, upload(h->L_round, S.L.round, h->stream));
+    NLE_CUDA(h, upload(h->U_off, S.U.off, h->stream));
+    NLE_CUDA(h, upload(h->U_w, S.U.width, h->stream));
+    NLE_CUDA(h, upload(h->U_col, S.U.col, h->stream));
+    NLE_CUDA(h, upload(h->U_val, S.U.val, h->stream));
+    NLE_CUDA(h, upload(h->U_round, S.U.round, h->stream));
+    NLE_CUDA(h, upload(h->d_diag, S.diag, h->stream));
   }
-  NLE_CUDA(h, upload(h->d_perm, h->perm));
-  NLE_CUDA(h, upload(h->d_iperm, h->iperm));
+  NLE_CUDA(h, upload(h->d_perm, h->perm, h->stream));
+  NLE_CUDA(h, upload(h->d_iperm, h->iperm, h->stream));
   const int64_t ext = h->npad + 32 * h->vw;
-  NLE_CUDA(h, dalloc(h->vecs, (size_t)(8 * h->npad + 2 * ext) * tsz));
-  NLE_CUDA(h, dalloc(h->vec64, (size_t)5 * h->npad * 8));
-  NLE_CUDA(h, dalloc(h->dS, (size_t)h->npad * KMAX * tsz));
-  NLE_CUDA(h, dalloc(h->dR, (size_t)h->npad * KMAX * tsz));
-  NLE_CUDA(h, dalloc(h->part, (size_t)2 * RED_MAX * h->grid * 8));
-  NLE_CUDA(h, dalloc(h->state, sizeof(State)));
-  NLE_CUDA(h, dalloc(h->scratch, (size_t)2 * h->n * 8));
+  NLE_CUDA(h, dalloc(h->vecs, (size_t)(8 * h->npad + 2 * ext) * tsz, h->stream));
+  NLE_CUDA(h, dalloc(h->vec64, (size_t)5 * h->npad * 8, h->stream));
+  NLE_CUDA(h, dalloc(h->dS, (size_t)h->npad * KMAX * tsz, h->stream));
+  NLE_CUDA(h, dalloc(h->dR, (size_t)h->npad * KMAX * tsz, h->stream));
+  NLE_CUDA(h, dalloc(h->part, (size_t)2 * RED_MAX * h->grid * 8, h->stream));
+  NLE_CUDA(h, dalloc(h->state, sizeof(State), h->stream));
+  NLE_CUDA(h, dalloc(h->scratch, (size_t)2 * h->n * 8, h->stream));
   h->ldq = 0;
   nle_status s = ensure_q(h, 8);
   if (s != NLE_OK) return s;
+  NLE_CUDA(h, cudaStreamSynchronize(h->stream));
   h->factored = true;
   return NLE_OK;
 }
@@ -707,7 +715,7 @@ static nle_status solve_impl(nle_t h, int p, double tol, int max_newton, int max
   double *vout = on_dev ? V : nullptr;
   DBuf tmp;
   if (!on_dev) {
-    NLE_CUDA(h, dalloc(tmp, (size_t)p * h->n * 8));
+    NLE_CUDA(h, dalloc(tmp, (size_t)p * h->n * 8, h->stream));
     vout = tmp.as<double>();
   }
   k_output_vectors<<<p, 1024, 0, h->stream>>>(vout, D.Qt, h->d_iperm.as<int32_t>(), h->n, h->npad, D.st);
@@ -715,9 +723,10 @@ static nle_status solve_impl(nle_t h, int p, double tol, int max_newton, int max
   NLE_CUDA(h, cudaGetLastError());
   if (!on_dev) NLE_CUDA(h, cudaMemcpyAsync(V, vout, (size_t)p * h->n * 8, cudaMemcpyDeviceToHost, h->stream));
   NLE_CUDA(h, cudaStreamSynchronize(h->stream));
-  if (on_dev)
-    NLE_CUDA(h, cudaMemcpy(lambda, st.lambda, p * sizeof(double), cudaMemcpyHostToDevice));
-  else
+  if (on_dev) {
+    NLE_CUDA(h, cudaMemcpyAsync(lambda, st.lambda, p * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    NLE_CUDA(h, cudaStreamSynchronize(h->stream));
+  } else
     memcpy(lambda, st.lambda, p * sizeof(double));
   h->lambda.assign(st.lambda, st.lambda + p);
   h->solved = true;
@@ -866,12 +875,12 @@ static nle_status backward_impl(nle_t h, const double *gl, const double *gV, dou
     std::vector<int32_t> er(nnz);
     for (int64_t i = 0; i < n; i++)
       for (int64_t e = h->rowptr[i]; e < h->rowptr[i + 1]; e++) er[e] = (int32_t)i;
-    NLE_CUDA(h, upload(h->d_erow, er));
-    NLE_CUDA(h, upload(h->d_ecol, h->col));
+    NLE_CUDA(h, upload(h->d_erow, er, h->stream));
+    NLE_CUDA(h, upload(h->d_ecol, h->col, h->stream));
   }
   double *grad = grad_val;
   if (!on_dev) {
-    NLE_CUDA(h, dalloc(h->d_grad, (size_t)nnz * 8));
+    NLE_CUDA(h, dalloc(h->d_grad, (size_t)nnz * 8, h->stream));
     NLE_CUDA(h, cudaMemcpyAsync(h->d_grad.p, grad_val, nnz * 8, cudaMemcpyHostToDevice, h->stream));
     grad = h->d_grad.as<double>();
   }
@@ -945,7 +954,7 @@ static nle_status batch_impl(int count, nle_t *hs, int p, double tol, int max_ne
     nle_status s = ensure_q(h, p);
     if (s != NLE_OK) return s;
     const size_t tsz = sizeof(T);
-    if (h->dX0.bytes < (size_t)p * h->npad * tsz) NLE_CUDA(h0, dalloc(h->dX0, (size_t)p * h->npad * tsz));
+    if (h->dX0.bytes < (size_t)p * h->npad * tsz) NLE_CUDA(h0, dalloc(h->dX0, (size_t)p * h->npad * tsz, h->stream));
     Dev<T> D = make_dev<T>(h);
     T *x0 = h->dX0.as<T>();
     for (int j = 0; j < p; j++) {
@@ -969,9 +978,9 @@ static nle_status batch_impl(int count, nle_t *hs, int p, double tol, int max_ne
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return hs[a]->n > hs[b]->n; });
   const int ngroups = std::max(1, h0->nsm / G);
   DBuf d_devs, d_order, d_ctl;
-  NLE_CUDA(h0, upload(d_devs, devs));
-  NLE_CUDA(h0, upload(d_order, order));
-  NLE_CUDA(h0, dalloc(d_ctl, (size_t)(1 + 3 * ngroups) * sizeof(int)));
+  NLE_CUDA(h0, upload(d_devs, devs, h0->stream));
+  NLE_CUDA(h0, upload(d_order, order, h0->stream));
+  NLE_CUDA(h0, dalloc(d_ctl, (size_t)(1 + 3 * ngroups) * sizeof(int), h0->stream));
   Batch<T> B;
   B.devs = d_devs.as<Dev<T>>();
   B.order = d_order.as<int>();
@@ -982,7 +991,11 @@ static nle_status batch_impl(int count, nle_t *hs, int p, double tol, int max_ne
   B.gbar = d_ctl.as<unsigned>() + 1;
   B.gslot = d_ctl.as<int>() + 1 + ngroups;
   B.gerr = d_ctl.as<int>() + 1 + 2 * ngroups;
-  B.group_spin_ns = (long long)(60.0 * 1e9);
+  // CTAs of a group that a small problem leaves idle wait in the group
+  // barrier for that whole problem: their limit is the handle's wait limit
+  // scaled by the grid barriers of a whole solve (every eigenpair, both
+  // phases), at least the barrier limit itself
+  B.group_spin_ns = (long long)(h0->opt.spin_timeout_s * 1e9 * 64.0 * p);
   Opts O = make_opts(h0, tol, max_newton, max_pcg);
   void *fn = kernel_ptr<T>(K_BATCH, rpc);
   if (!fn) return fail(h0, NLE_ERR_ARG, "no kernel instance for this size");

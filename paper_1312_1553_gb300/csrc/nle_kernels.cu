@@ -481,7 +481,13 @@ __device__ bool pcg_solve(const Dev<T> &D, const Opts &O, Shared &sh, Ctl &ctl, 
     }
     const double gn = sqrt(sh.sc[0]);
     const double rs = sh.sc[1], sg = sh.sc[2], ss = sh.sc[3];
-    // eq. "residual" without a product with A (see oracle/solver.py)
+    // Exit (iii), eq. "residual", without a product with A.  With x = u + s,
+    // s orthogonal to Q (u is a column of Q), (A - theta I) u = r and
+    // J s = -r - g, and neglecting v_i^T (A - theta I) s for the converged
+    // v_i: ||A x - theta x||^2 = ||g||^2 + (r^T s)^2,
+    // x^T (A - theta I) x = r^T s - s^T g, so rho - theta =
+    // (r^T s - s^T g) / (1 + ||s||^2) and ||A x - rho x||^2 =
+    // ||A x - theta x||^2 - (rho - theta)^2 (1 + ||s||^2).
     const double x2 = 1.0 + ss;
     const double dth = (rs - sg) / x2;
     const double e2 = gn * gn + rs * rs - dth * dth * x2;

@@ -7,6 +7,7 @@
 // the runtime for the array's device address once per device.
 #include <cuda_runtime.h>
 
+#include <cstdint>
 #include <cstdio>
 #include <mutex>
 #include <string>
@@ -115,6 +116,15 @@ extern "C" nle_status nle_ic_apply_noalloc(int64_t n, const int32_t *Lrp, const 
     nle::set_global_error("nle_ic_apply_noalloc: NULL pointer");
     return NLE_ERR_ARG;
   }
+  {
+    // c is written (with the not-yet-computed marker) before g is read, so
+    // the two may not share memory
+    const uintptr_t g0 = (uintptr_t)g, c0 = (uintptr_t)c, nb = (uintptr_t)n * sizeof(double);
+    if (g0 < c0 + nb && c0 < g0 + nb) {
+      nle::set_global_error("nle_ic_apply_noalloc: g and c overlap (in-place application is not supported)");
+      return NLE_ERR_ARG;
+    }
+  }
   cudaStream_t s = (cudaStream_t)stream;
   double *z = nullptr;
   cudaError_t e = scratch_address(&z);
@@ -132,6 +142,9 @@ extern "C" nle_status nle_ic_apply_noalloc(int64_t n, const int32_t *Lrp, const 
     return NLE_ERR_CUDA;
   }
   const long long lim = (long long)(2.0 * 2.1e9);  // ~2 s at the maximum SM clock
+  // clear a launch error left pending by earlier work of the caller, so
+  // that the check below reports this call's own launches
+  (void)cudaGetLastError();
   k_na_fill<<<256, 256, 0, s>>>(z, c, n, err);
   e = cudaGetLastError();
   int64_t nn = n;

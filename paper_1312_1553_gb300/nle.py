@@ -18,6 +18,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libnle.so")
 
 NLE_OK = 0
+NLE_ERR_ARG, NLE_ERR_CSR, NLE_ERR_NOCONV, NLE_ERR_TIMEOUT = 1, 2, 5, 8
 STATUS = {0: "NLE_OK", 1: "NLE_ERR_ARG", 2: "NLE_ERR_CSR", 3: "NLE_ERR_NOT_SPD", 4: "NLE_ERR_BREAKDOWN",
           5: "NLE_ERR_NOCONV", 6: "NLE_ERR_CUDA", 7: "NLE_ERR_OOM", 8: "NLE_ERR_TIMEOUT", 9: "NLE_ERR_STATE",
           10: "NLE_ERR_NO_DEVICE"}

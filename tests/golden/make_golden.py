@@ -6,8 +6,10 @@ of ``workloads/``; nothing here calls the CUDA library.  Usage:
     python tests/golden/make_golden.py diff3d7_100 [more workload names]
 
 Each run writes tests/golden/<name>.json with the eigenvalues, the oracle's
-iteration counts, and a seeded sample of eigenvector entries (sign
-convention: entry of largest modulus positive).
+iteration counts, a seeded sample of eigenvector entries and a seeded
+CountSketch (workloads.count_sketch) of every eigenvector (sign convention:
+entry of largest modulus positive), plus the loss gradient with respect to
+the cell or element coefficients for the 2D diffusion and hex workloads.
 """
 import json
 import os
@@ -47,6 +49,29 @@ def kappa_gradient(A, lam, V, opt):
                 grad_kappa_norm=float(np.linalg.norm(gk)))
 
 
+def hex_kappa_gradient(A, lam, V):
+    """Gradient of loss = sum lambda_j with respect to the element
+    coefficients of the hex stiffness: d lambda_j / d A_ab = v_ja v_jb (the
+    oracle's adjoint with no eigenvector term), carried through the assembly
+    by torch CPU autograd; sampled at 64 seeded elements."""
+    import torch
+
+    p = len(lam)
+    gA = O.adjoint_grad(A, lam, V, np.ones(p), None, None)
+    kappa = torch.tensor(A.meta["kappa"], dtype=torch.float64, requires_grad=True)
+    vals = W.hex_poisson_values_torch(kappa)
+    (gk,) = torch.autograd.grad(vals, kappa, grad_outputs=torch.tensor(gA))
+    gk = gk.numpy().ravel()
+    rng = W.rng_for(5252)
+    elems = np.sort(rng.choice(gk.size, size=64, replace=False))
+    return dict(loss=float(lam.sum()), grad_elems=[int(e) for e in elems], grad_kappa=[float(gk[e]) for e in elems],
+                grad_kappa_norm=float(np.linalg.norm(gk)),
+                grad_kappa_euler=float(A.meta["kappa"].ravel() @ gk))
+
+
+SKETCH_K = 256
+
+
 def main(names):
     for name in names:
         A, st = W.workload(name)
@@ -65,8 +90,15 @@ def main(names):
                    oracle_seconds=sec, oracle_stats={k: stats[k] for k in
                                                      ("dacg_its", "outer_its", "pcg_its", "converged", "final_res",
                                                       "ascending", "nnz_L", "sigma")})
+        # CountSketch of every eigenvector (sign convention applied): the
+        # full-size tests compare sketches, which estimate ||v_gpu - v_oracle||
+        bucket, sign = W.count_sketch_hash(A.n, SKETCH_K, st["seed"])
+        out.update(sketch_K=SKETCH_K, sketch_seed=st["seed"],
+                   sketch_V=[[float(x) for x in W.count_sketch(V[:, j], bucket, sign, SKETCH_K)] for j in range(p)])
         if name.startswith("diff2d5"):
             out.update(kappa_gradient(A, lam, V, opt))
+        if name.startswith("hex27"):
+            out.update(hex_kappa_gradient(A, lam, V))
         with open(os.path.join(HERE, f"{name}.json"), "w") as fh:
             json.dump(out, fh, indent=1)
         print(name, sec, lam)

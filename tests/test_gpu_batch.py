@@ -97,3 +97,61 @@ def test_batch_groups_of_eight_fp64(nle):
     np.testing.assert_allclose(lams[1].cpu().numpy(), lref, rtol=1e-10)
     for s in solvers:
         s.close()
+
+
+def test_batch_on_non_blocking_stream(nle):
+    """Handles created on a non-blocking stream (which does not wait for the
+    legacy default stream): the set-up uploads, the batch's control words and
+    the launch are all ordered on that stream, and the results equal the
+    single-problem solves on the same stream."""
+    import torch
+
+    stream = torch.cuda.Stream()
+    sizes = [3300, 2100, 4800]
+    mats = [W.geometric_graph_laplacian(n, 960 + i) for i, n in enumerate(sizes)]
+    p = 3
+    with torch.cuda.stream(stream):
+        solvers, X0s = [], []
+        for i, A in enumerate(mats):
+            s = nle.Eigensolver(A, dict(precision=nle.NLE_FP64, grid_ctas=4), stream=stream)
+            s.factor_ic(30, 1e-2)
+            solvers.append(s)
+            X0s.append(W.start_vectors(A.n, p, 740 + i))
+        lams, Vs, per = nle.batch_solve(solvers, p, 1e-8, 400, 20, X0s)
+        assert all(x == 0 for x in per), per
+        for i, A in enumerate(mats):
+            l1, _, _ = solvers[i].solve(p, 1e-8, 400, 20, X0s[i])
+            np.testing.assert_allclose(lams[i].cpu().numpy(), l1.cpu().numpy(), rtol=1e-10)
+            assert abs(lams[i][0].item() - 1e-3) <= 1e-12
+    stream.synchronize()
+    for s in solvers:
+        s.close()
+
+
+def test_batch_bounded_wait_reports_timeout_and_context_survives(nle):
+    """A wait limit far below any real wait makes every problem of the batch
+    report NLE_ERR_TIMEOUT (problem barriers and the group barriers are all
+    bounded); the kernel returns on its own and the next batch in the same
+    process solves normally."""
+    mats = [W.geometric_graph_laplacian(n, 970 + i) for i, n in enumerate([2500, 3500])]
+    p = 2
+    X0s = [W.start_vectors(A.n, p, 760 + i) for i, A in enumerate(mats)]
+    bad = []
+    for A in mats:
+        s = nle.Eigensolver(A, dict(precision=nle.NLE_MIXED, grid_ctas=4, spin_timeout_s=1e-9))
+        s.factor_ic(30, 1e-2)
+        bad.append(s)
+    with pytest.raises(nle.NLEError) as e:
+        nle.batch_solve(bad, p, 1e-8, 100, 20, X0s)
+    assert e.value.code == nle.NLE_ERR_TIMEOUT
+    for s in bad:
+        s.close()
+    good = []
+    for A in mats:
+        s = nle.Eigensolver(A, dict(precision=nle.NLE_MIXED, grid_ctas=4))
+        s.factor_ic(30, 1e-2)
+        good.append(s)
+    lams, Vs, per = nle.batch_solve(good, p, 1e-8, 100, 20, X0s)
+    assert all(x == 0 for x in per), per
+    for s in good:
+        s.close()

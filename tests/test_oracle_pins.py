@@ -557,6 +557,69 @@ def test_kappa_gradient_fd_and_euler_identity():
         assert abs(fd - gk.flat[c]) <= 1e-6 * scale, (c, fd, gk.flat[c])
 
 
+def test_hex_torch_assembly_matches_numpy_assembly():
+    """The differentiable hex assembly reproduces the stored values of the
+    27-point stiffness bit for bit (so gradients with respect to entries map
+    onto element coefficients)."""
+    import torch
+
+    A = W.hex_poisson_27pt(5, seed=7)
+    vals = W.hex_poisson_values_torch(torch.tensor(A.meta["kappa"], dtype=torch.float64))
+    np.testing.assert_array_equal(vals.numpy(), A.val)
+
+
+def test_hex_element_gradient_fd_and_euler_identity():
+    """Element-coefficient gradient of loss = sum lambda_j for the hex
+    stiffness: the oracle adjoint (d lambda_j / d A_ab = v_ja v_jb) chained
+    through the torch assembly against central differences of a dense
+    eigendecomposition (step 1e-6 kappa_e) at every element, and the Euler
+    identity sum_e kappa_e dL/dkappa_e = sum_j lambda_j."""
+    import torch
+
+    A = W.hex_poisson_27pt(3, seed=31)  # 27 unknowns, 64 elements
+    kappa = A.meta["kappa"]
+    p = 4
+
+    def loss_of(kap):
+        lam = np.linalg.eigvalsh(dense(W.hex_poisson_from_kappa(kap)))
+        return lam[:p].sum()
+
+    lam, Vv = np.linalg.eigh(dense(A))
+    V = np.stack([O.fix_sign(Vv[:, j]) for j in range(p)], axis=1)
+    gA = O.adjoint_grad(A, lam[:p], V, np.ones(p), None, None)
+    kt = torch.tensor(kappa, dtype=torch.float64, requires_grad=True)
+    (gk,) = torch.autograd.grad(W.hex_poisson_values_torch(kt), kt, grad_outputs=torch.tensor(gA))
+    gk = gk.numpy()
+    assert abs((kappa * gk).sum() - lam[:p].sum()) <= 1e-12 * lam[:p].sum()
+    scale = np.abs(gk).max()
+    for e in range(kappa.size):
+        h = 1e-6 * kappa.flat[e]
+        kp = kappa.copy()
+        kp.flat[e] += h
+        km = kappa.copy()
+        km.flat[e] -= h
+        fd = (loss_of(kp) - loss_of(km)) / (2 * h)
+        assert abs(fd - gk.flat[e]) <= 1e-6 * scale, (e, fd, gk.flat[e])
+
+
+def test_count_sketch_estimates_vector_distance():
+    """The CountSketch the full-size tests compare eigenvectors through:
+    linear, and ||S x|| within 25 % of ||x|| for spread-out vectors at
+    K = 256 (its relative spread is about sqrt(2/K) = 9 %)."""
+    n, K = 200_000, 256
+    bucket, sign = W.count_sketch_hash(n, K, 5)
+    rng = W.rng_for(77)
+    x = rng.standard_normal(n)
+    y = rng.standard_normal(n)
+    np.testing.assert_allclose(W.count_sketch(x + 2 * y, bucket, sign, K),
+                               W.count_sketch(x, bucket, sign, K) + 2 * W.count_sketch(y, bucket, sign, K),
+                               rtol=1e-12, atol=1e-9)
+    for t in range(20):
+        z = W.rng_for(100 + t).standard_normal(n) * np.exp(W.rng_for(200 + t).standard_normal(n))
+        r = np.linalg.norm(W.count_sketch(z, bucket, sign, K)) / np.linalg.norm(z)
+        assert 0.75 <= r <= 1.25, (t, r)
+
+
 def test_full_bfgs_update_pairs_and_closed_form():
     """Section 3's full BFGS update (y_k = r_{k+1} - r_k): the method still
     reaches the closed-form spectrum of the anisotropic Laplacian; every

@@ -1,9 +1,13 @@
 """The allocation-free entry point nle_ic_apply_noalloc, called through the C
 ABI, gives the same c = (L L^T)^{-1} g as the handle-based nle_apply_prec
-(k = 0 pairs, no projection), on two calls in a row.
+(k = 0 pairs, no projection) and as the oracle's P0hat, on two calls in a
+row; it rejects overlapping g and c and reports an entry that is not
+strictly triangular.
 
 The entry point exists for callers that cannot allocate device memory when
-they apply the preconditioner; its scratch is a fixed array inside the
+they apply the preconditioner (code inside another framework's memory pool,
+real-time loops that cannot take cudaMalloc's synchronisation, programs that
+allocate only at start-up); its scratch is a fixed array inside the
 library.  This file is collected last on purpose."""
 import ctypes
 
@@ -37,6 +41,8 @@ def _split_factor(F, n):
 def test_no_alloc_ic_apply_matches_handle_entry_point():
     import torch
 
+    import oracle as O
+    from oracle.solver import p0hat
     from paper_1312_1553_gb300 import _build, nle
 
     _build.build()
@@ -46,6 +52,7 @@ def test_no_alloc_ic_apply_matches_handle_entry_point():
     assert n <= nle.NLE_NOALLOC_MAX_N
     s = nle.Eigensolver(A, dict(precision=nle.NLE_FP64))
     s.factor_ic(st["lfil"], st["tau_ic"])
+    ic = O.ic_factor(A, st["lfil"], st["tau_ic"])
     parts = _split_factor(s.get_factor(), n)
     dev = [torch.from_numpy(a).cuda() for a in parts]
     stream = torch.cuda.current_stream()
@@ -62,6 +69,24 @@ def test_no_alloc_ic_apply_matches_handle_entry_point():
         got = c.cpu().numpy()
         err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
         assert err <= 1e-11, err
+        want = p0hat(ic, g)  # the oracle's (L L^T)^{-1} g
+        err = np.linalg.norm(got - want) / np.linalg.norm(want)
+        assert err <= 1e-11, err
+    # in-place use (c overlapping g) is rejected before any work
+    rc = nle.nle_ic_apply_noalloc(n, ptr[0], ptr[1], ptr[2], ptr[3], ptr[4], ptr[5], ptr[6],
+                                  ctypes.c_void_p(gd.data_ptr()), ctypes.c_void_p(gd.data_ptr() + 8),
+                                  ctypes.c_void_p(stream.cuda_stream))
+    assert rc == nle.NLE_ERR_ARG and "overlap" in nle.nle_last_error(None)
+    # an entry on the diagonal in the strictly lower part is skipped (before
+    # any load) and reported
+    Lcol_bad = parts[1].copy()
+    r = int(np.flatnonzero(np.diff(parts[0]) > 0)[0])
+    Lcol_bad[parts[0][r]] = r
+    bad = torch.from_numpy(Lcol_bad).cuda()
+    rc = nle.nle_ic_apply_noalloc(n, ptr[0], ctypes.c_void_p(bad.data_ptr()), ptr[2], ptr[3], ptr[4], ptr[5],
+                                  ptr[6], ctypes.c_void_p(gd.data_ptr()), ctypes.c_void_p(c.data_ptr()),
+                                  ctypes.c_void_p(stream.cuda_stream))
+    assert rc == nle.NLE_ERR_CSR, nle.nle_last_error(None)
     s.close()
     # beyond the fixed scratch: rejected before any memory is touched
     rc = nle.nle_ic_apply_noalloc(nle.NLE_NOALLOC_MAX_N + 1, *([None] * 9), None)

@@ -359,17 +359,13 @@ def hex8_reference_stiffness() -> np.ndarray:
     return K
 
 
-def hex_poisson_27pt(m: int = 96, sigma: float = 1.0, seed: int = BASE_SEED + 5) -> CSR:
-    """27-point stiffness on the m^3 interior nodes of an (m+1)^3 hex mesh.
-
-    Element coefficients kappa_e = exp(sigma N(0,1)); mesh width h = 1/(m+1),
-    so the element matrix is h*kappa_e*K_ref; boundary nodes are eliminated
-    (homogeneous Dirichlet).  All 27 couplings are kept in the pattern even
-    where the assembled value is (numerically) zero.
-    """
-    rng = rng_for(seed)
-    ne = m + 1
-    kappa = np.exp(sigma * rng.standard_normal((ne, ne, ne)))  # (ez, ey, ex)
+def _hex_coefs(kappa, zeros):
+    """Stencil coefficients of the hex stiffness, one (m, m, m) array per
+    offset (dz, dy, dx) in lexicographic order, from the element
+    coefficients kappa ((m+1)^3, numpy or torch: the same operations in the
+    same order, so both give identical values)."""
+    ne = kappa.shape[0]
+    m = ne - 1
     Kr = hex8_reference_stiffness()
     h = 1.0 / ne
     offsets = []
@@ -377,7 +373,7 @@ def hex_poisson_27pt(m: int = 96, sigma: float = 1.0, seed: int = BASE_SEED + 5)
     for dz in (-1, 0, 1):
         for dy in (-1, 0, 1):
             for dx in (-1, 0, 1):
-                c = np.zeros((m, m, m))
+                c = zeros((m, m, m))
                 # elements around node N = (K, J, I) in 1..m: e = N - a, a in {0,1}^3
                 for az in (0, 1):
                     for ay in (0, 1):
@@ -388,11 +384,57 @@ def hex_poisson_27pt(m: int = 96, sigma: float = 1.0, seed: int = BASE_SEED + 5)
                             la = ax + 2 * ay + 4 * az
                             lb = bx + 2 * by + 4 * bz
                             ke = kappa[1 - az:ne - az, 1 - ay:ne - ay, 1 - ax:ne - ax]
-                            c += ke * (h * Kr[la, lb])
+                            c = c + ke * float(h * Kr[la, lb])
                 offsets.append((dz, dy, dx))
                 coefs.append(c)
-    return _stencil_csr((m, m, m), offsets, coefs, name=f"hex27_{m}",
+    return offsets, coefs, h
+
+
+def hex_poisson_from_kappa(kappa: np.ndarray, name: str = "") -> CSR:
+    """27-point stiffness on the m^3 interior nodes of an (m+1)^3 hex mesh
+    with element coefficients kappa (shape (m+1)^3, index (ez, ey, ex)).
+
+    Mesh width h = 1/(m+1), so the element matrix is h*kappa_e*K_ref;
+    boundary nodes are eliminated (homogeneous Dirichlet).  All 27 couplings
+    are kept in the pattern even where the assembled value is (numerically)
+    zero.
+    """
+    m = kappa.shape[0] - 1
+    offsets, coefs, h = _hex_coefs(kappa, np.zeros)
+    return _stencil_csr((m, m, m), offsets, coefs, name=name or f"hex27_{m}",
                         meta=dict(shape=(m, m, m), kappa=kappa, h=h))
+
+
+def hex_poisson_values_torch(kappa):
+    """The stored values of hex_poisson_from_kappa(kappa), in its CSR order,
+    as a differentiable function of the torch tensor kappa ((m+1)^3).
+
+    Used to carry gradients with respect to the matrix entries over to the
+    element coefficients (chain rule through the assembly)."""
+    import torch
+
+    m = kappa.shape[0] - 1
+    offsets, coefs, _ = _hex_coefs(kappa, lambda s: torch.zeros(s, dtype=kappa.dtype))
+    idx = np.indices((m, m, m)).reshape(3, -1)
+    masks = []
+    for o in offsets:
+        ok = np.ones(m ** 3, dtype=bool)
+        for d in range(3):
+            q = idx[d] + o[d]
+            ok &= (q >= 0) & (q < m)
+        masks.append(ok)
+    V = torch.stack([c.reshape(-1) for c in coefs], dim=1)
+    M = torch.from_numpy(np.stack(masks, axis=1))
+    return V[M]
+
+
+def hex_poisson_27pt(m: int = 96, sigma: float = 1.0, seed: int = BASE_SEED + 5) -> CSR:
+    """hex_poisson_from_kappa with element coefficients kappa_e =
+    exp(sigma N(0,1)) on an (m+1)^3 element grid (m^3 unknowns)."""
+    rng = rng_for(seed)
+    ne = m + 1
+    kappa = np.exp(sigma * rng.standard_normal((ne, ne, ne)))  # (ez, ey, ex)
+    return hex_poisson_from_kappa(kappa, name=f"hex27_{m}")
 
 
 # ---------------------------------------------------------------------------
@@ -438,6 +480,24 @@ def permute(A: CSR, perm) -> CSR:
     B.sort_indices()
     return CSR(A.n, B.indptr.astype(np.int64), B.indices.astype(np.int32), B.data.copy(),
                name=A.name + "_perm", meta=dict(A.meta))
+
+
+def count_sketch_hash(n: int, K: int, seed: int):
+    """Seeded CountSketch of R^n into R^K: a bucket in [0, K) and a sign
+    +-1 for every coordinate.  Used to compare long vectors (eigenvectors
+    at n ~ 1e6) through K numbers: for x in R^n the sketch S x has
+    E ||S x||^2 = ||x||^2, with relative spread about sqrt(2/K) for vectors
+    whose mass is spread over many coordinates."""
+    rng = rng_for(seed + 9_000_000)
+    bucket = rng.integers(0, K, size=n)
+    sign = rng.integers(0, 2, size=n).astype(np.float64) * 2.0 - 1.0
+    return bucket, sign
+
+
+def count_sketch(x: np.ndarray, bucket: np.ndarray, sign: np.ndarray, K: int) -> np.ndarray:
+    """S x for the hash of count_sketch_hash: y[b] = sum over i with
+    bucket[i] = b of sign[i] x[i]."""
+    return np.bincount(bucket, weights=sign * np.asarray(x, dtype=np.float64), minlength=K)
 
 
 def start_vectors(n: int, p: int, seed: int) -> np.ndarray:
