@@ -31,7 +31,9 @@ sys.path.insert(0, ROOT)
 
 WORKLOAD = "diff3d7_100"
 WORKLOAD_P = 10
-CPU_SAMPLE_PAIRS = 3  # bounded oracle sample: the first eigenpairs of the workload
+CPU_SAMPLE_PAIRS = 3  # bounded oracle sample of the CPU baseline: the first eigenpairs of the workload
+REF_STEP_PAIRS = 1    # the reference arm's step: the first eigenpair (a few seconds of oracle work)
+FP64_STEPS = 3        # timed steps of the plain FP64 arm (its warm-up: 1 step)
 METRIC = "eigenpairs/s at n=1e6, rel. residual 1e-8"
 DESCRIPTION = {
     "diff3d7_100": "3D 7-point diffusion 100^3, exp(Gaussian field) faces",
@@ -52,6 +54,7 @@ def parse():
                          "for FP32 inner solves)")
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 arm (profiling runs)")
     ap.add_argument("--skip-e2e", action="store_true", help="profiling runs: skip the host-buffer pass")
     ap.add_argument("--pairs", type=int, default=0, help="profiling runs: solve only the first P eigenpairs")
     ap.add_argument("--trsv-warps", type=int, default=0, help="0 = library default")
@@ -63,6 +66,11 @@ def parse():
                     help="outer step cap; 0 = the workload's (the paper's ITMAX = 100; 400 for workloads with "
                          "eigenvalue clusters)")
     ap.add_argument("--spin-timeout", type=float, default=0.0, help="0 = library default (seconds)")
+    ap.add_argument("--halo", type=int, default=-1, help="level schedule: -1 library default; 0 solving warps read "
+                                                         "off-slab values themselves; d >= 1 a copy warp stages those "
+                                                         "at least d levels back")
+    ap.add_argument("--schedule", default="auto", choices=["auto", "level", "chain"],
+                    help="schedule of the triangular solves (auto = timed at set-up, the faster kept)")
     ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--sample-eigenpairs", type=int, default=1, help=argparse.SUPPRESS)
     return ap.parse_args()
@@ -133,11 +141,27 @@ def run_cpu_sample(workload: str, npairs: int) -> dict:
     return json.loads(r.stdout.strip().splitlines()[-1])
 
 
+def golden(workload: str):
+    """The stored oracle run of a workload (tests/golden/<name>.json, written
+    by tests/golden/make_golden.py from the oracle alone), or None."""
+    try:
+        with open(os.path.join(ROOT, "tests", "golden", f"{workload}.json")) as fh:
+            return json.load(fh)
+    except Exception:
+        return None
+
+
 def cpu_baseline_entry(res: dict, workload: str) -> dict:
-    return dict(value=res["eigenpairs"] / res["seconds"], unit=UNIT, cores=1, kind="oracle",
-                sample=f"oracle (numpy + plain C, FP64, 1 thread) on eigenpairs 1-{res['eigenpairs']} of {workload} "
-                       f"({res['seconds']:.1f} s, IC set-up excluded; later eigenpairs cost more, so this "
-                       f"overstates the oracle's rate for all {WORKLOAD_P} pairs)")
+    e = dict(value=res["eigenpairs"] / res["seconds"], unit=UNIT, cores=1, nproc=os.cpu_count(), kind="oracle",
+             sample=f"oracle (numpy + plain C, FP64, 1 thread) on eigenpairs 1-{res['eigenpairs']} of {workload} "
+                    f"({res['seconds']:.1f} s, IC set-up excluded); later eigenpairs cost more (more deflation "
+                    f"columns, more Newton steps), so the sample overstates the oracle's rate for all pairs")
+    g = golden(workload)
+    if g and g.get("oracle_seconds"):
+        e["full_run"] = dict(value=g["p"] / g["oracle_seconds"], seconds=g["oracle_seconds"], eigenpairs=g["p"],
+                             where="the stored oracle run of tests/golden (all pairs, 1 process; measured on the "
+                                   "development host, not on this machine)")
+    return e
 
 
 def reference_arm(args):
@@ -146,18 +170,19 @@ def reference_arm(args):
         return 0
     times = []
     for i in range(args.warmup + args.steps):
-        res = run_cpu_sample(args.workload, CPU_SAMPLE_PAIRS)
+        res = run_cpu_sample(args.workload, REF_STEP_PAIRS)
         if i >= args.warmup:
             times.append(res["seconds"])
     total = sum(times)
-    value = CPU_SAMPLE_PAIRS * args.steps / total
+    value = REF_STEP_PAIRS * args.steps / total
     line = dict(impl="reference", metric=METRIC, value=value, unit=UNIT, n_gpus=args.gpus, steps=args.steps,
                 warmup=args.warmup, ms_per_step=1000 * total / args.steps, higher_is_better=True, scaling="weak",
                 vs_baseline=None, dtype="f64", data="synthetic",
                 config=dict(workload=args.workload,
-                            sample=f"eigenpairs 1-{CPU_SAMPLE_PAIRS} per step (DACG + Newton), IC set-up excluded"),
-                cpu_baseline=dict(value=value, unit=UNIT, cores=1, kind="oracle",
-                                  sample=f"eigenpairs 1-{CPU_SAMPLE_PAIRS} of the workload per step, 1 thread"),
+                            sample=f"eigenpair 1-{REF_STEP_PAIRS} per step (DACG + Newton), IC set-up excluded"),
+                cpu_baseline=dict(value=value, unit=UNIT, cores=1, nproc=os.cpu_count(), kind="oracle",
+                                  sample=f"eigenpair 1-{REF_STEP_PAIRS} of the workload per step, 1 thread (the "
+                                         f"cheapest eigenpair: this overstates the rate over all pairs)"),
                 e2e=dict(value=value, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
     print(json.dumps(line), flush=True)
     return 0
@@ -324,7 +349,8 @@ def batch_main(args, world, rank, local, cpu):
         solvers = []
         for A in mats:
             # FP64 needs 8 CTAs per problem for the largest graphs (n = 60,000)
-            s = nle.Eigensolver(A, dict(precision=prec, grid_ctas=4 if prec == nle.NLE_MIXED else 8), stream=stream)
+            s = nle.Eigensolver(A, dict(precision=prec, grid_ctas=4 if prec == nle.NLE_MIXED else 8,
+                                        trsv_schedule=nle.NLE_SCHED_LEVEL), stream=stream)
             s.factor_ic(30, 1e-2)
             solvers.append(s)
         ic_seconds = time.perf_counter() - t0
@@ -479,6 +505,10 @@ def main():
     opts["ordering"] = {"natural": nle.NLE_ORDER_NATURAL, "mc1": nle.NLE_ORDER_MULTICOLOR1,
                         "mc2": nle.NLE_ORDER_MULTICOLOR2}[args.ordering]
     opts["bfgs_update"] = nle.NLE_BFGS_FULL if args.bfgs == "full" else nle.NLE_BFGS_SIMPLIFIED
+    opts["trsv_schedule"] = {"auto": nle.NLE_SCHED_AUTO, "level": nle.NLE_SCHED_LEVEL,
+                             "chain": nle.NLE_SCHED_CHAIN}[args.schedule]
+    if args.halo >= 0:
+        opts["trsv_halo"] = args.halo
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         s = nle.Eigensolver(A, opts, stream=stream)
@@ -531,7 +561,40 @@ def main():
             _ = float(lam_h[0])
         e2e_sec = max(time.perf_counter() - t0, 1e-9)
         lam_dev = lam.cpu().numpy()
+        V_dev = V.cpu().numpy()
         s.close()
+        # the plain FP64 form of the same solve (the baseline of the mixed
+        # form's speed-up), same schedule option, fewer steps
+        fp64 = None
+        if prec == nle.NLE_MIXED and not args.no_fp64:
+            o64 = dict(opts, precision=nle.NLE_FP64)
+            s64 = nle.Eigensolver(A, o64, stream=stream)
+            s64.factor_ic(st["lfil"], st["tau_ic"])
+            lam64 = torch.empty(p, dtype=torch.float64, device="cuda")
+            V64 = torch.empty((p, A.n), dtype=torch.float64, device="cuda")
+
+            def step64():
+                stats = nle.nle_stats()
+                rc = nle.nle_solve(s64.h, p, st["tol"], max_newton, 20, nle._dptr(x0), nle._dptr(lam64),
+                                   nle._dptr(V64), stats, 1)
+                if rc != 0:
+                    raise nle.NLEError(rc, nle.nle_last_error(s64.h))
+                return nle.stats_dict(stats)
+
+            step64()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st64 = [step64() for _ in range(FP64_STEPS)]
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms64 = e0.elapsed_time(e1)
+            fp64 = dict(value=p * FP64_STEPS / (ms64 / 1000.0), unit=UNIT, ms_per_step=ms64 / FP64_STEPS,
+                        steps=FP64_STEPS, warmup=1, trsv_schedule=st64[-1]["trsv_schedule"],
+                        iterations=dict(pcg=st64[-1]["pcg_iterations"], dacg=st64[-1]["dacg_iterations"]))
+            lam64_h = lam64.cpu().numpy()
+            s64.close()
 
     # max over ranks
     t_max, e2e_max = max_over_ranks([ms / 1000.0, e2e_sec])
@@ -563,6 +626,23 @@ def main():
                 other=dict(kernel="k_dacg" if kern == "k_newton" else "k_newton",
                            achieved=((b_dacg if kern == "k_newton" else b_newton) / 1e9) /
                            (max(ms_dacg if kern == "k_newton" else ms_newton, 1e-9) / 1e3)))
+    # error against the stored FP64 oracle run: eigenvalues (relative) and
+    # eigenvectors (CountSketch estimate of ||v - v_oracle||, which is the
+    # angle between them to first order)
+    accuracy = None
+    g = golden(args.workload)
+    if g and g["p"] == p and "sketch_V" in g:
+        lam_g = np.array(g["lam"])
+        bucket, sign = W.count_sketch_hash(A.n, g["sketch_K"], g["sketch_seed"])
+        ang = []
+        for j in range(p):
+            sk = W.count_sketch(V_dev[j], bucket, sign, g["sketch_K"])
+            ref = np.array(g["sketch_V"][j])
+            ang.append(float(min(np.linalg.norm(sk - ref), np.linalg.norm(sk + ref))))
+        accuracy = dict(vs="stored FP64 oracle run (tests/golden)", max_rel_eig_err=float(np.max(np.abs(lam_dev - lam_g) / lam_g)),
+                        max_vec_angle_sketch=max(ang), vec_angle_sketch=ang)
+        if fp64 is not None:
+            fp64["max_rel_eig_err"] = float(np.max(np.abs(lam64_h - lam_g) / lam_g))
     metric = METRIC if args.workload == WORKLOAD else f"eigenpairs/s, {args.workload}, rel. residual {st['tol']:g}"
     line = dict(metric=metric, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
                 ms_per_step=1000 * t_max / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
@@ -571,6 +651,8 @@ def main():
                             n=A.n, nnz=A.nnz, p=p, lfil=st["lfil"], tau_ic=st["tau_ic"], tol=st["tol"],
                             precision="FP32 bulk + FP64 outer step" if prec == nle.NLE_MIXED else "FP64",
                             nnz_L=nnz_l, nlev_L=F["nlevL"], ordering=args.ordering, bfgs=args.bfgs, ic_seconds=ic_seconds,
+                            trsv_schedule=all_stats[-1]["trsv_schedule"], schedule_request=args.schedule, halo=args.halo,
+                            tune_ms=all_stats[-1]["tune_ms"], strands=all_stats[-1]["strands"],
                             l2="working set > 129 MB L2 (no flush needed)",
                             parallelism=f"replicas{world}" if world > 1 else "single GPU"),
                 roofline=roof, cpu_baseline=cpu,
@@ -579,7 +661,8 @@ def main():
                 clocks=clocks, gpu_launches=int(sum(x["kernel_launches"] for x in all_stats)),
                 phase_ms=dict(dacg=ms_dacg / args.steps, newton=ms_newton / args.steps),
                 iterations=dict(pcg=its / args.steps, dacg=dits / args.steps),
-                lambda_first=float(lam_dev[0]))
+                lambda_first=float(lam_dev[0]), accuracy=accuracy, fp64=fp64,
+                mixed_over_fp64=(value / fp64["value"]) if fp64 else None)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

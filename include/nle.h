@@ -101,7 +101,34 @@ typedef struct {
   int ordering;          /* NLE_ORDER_NATURAL (default) or a multicolour ordering, see
                             nle_multicolor_order; applied before the IC factor */
   int bfgs_update;       /* NLE_BFGS_SIMPLIFIED (default) or NLE_BFGS_FULL */
+  int trsv_schedule;     /* NLE_SCHED_AUTO (default), NLE_SCHED_LEVEL or NLE_SCHED_CHAIN */
+  int trsv_halo;         /* level schedule, natural ordering: 0 (default) every solving warp
+                            reads the values its slab needs from other slabs in global
+                            memory itself; d >= 1: those that lie at least d levels below
+                            the row needing them are copied into shared memory by the
+                            CTA's last warp as they are published (when the lists fit in
+                            192 KB with the slab buffers) */
+  int halo_window;       /* halo copy warp: values in flight per lane, 1..8 (default 4) */
+  int halo_backoff_ns;   /* halo copy warp: pause after a sweep that moved nothing (default 0) */
 } nle_options;
+
+/* Schedule of the triangular solves of Phat_0 = (L L^T)^{-1} (Section 2).
+ * Both give the same solution (up to rounding order); they differ in how
+ * the rows are dealt to the GPU's warps:
+ *   NLE_SCHED_LEVEL  rows of each CTA's slab sorted by level of L, groups
+ *                    of 4 same-level rows per warp step;
+ *   NLE_SCHED_CHAIN  the factored matrix's own row order; runs of rows in
+ *                    which each row depends on its predecessor (the grid
+ *                    lines of a stencil matrix in natural order) stay on one
+ *                    warp, which resolves that dependency in registers;
+ *                    needs the natural ordering;
+ *   NLE_SCHED_AUTO   nle_factor_ic times one application of (L L^T)^{-1}
+ *                    with each schedule on the device and keeps the faster
+ *                    (the level schedule under a multicolour ordering).
+ * The choice and the timings are reported in nle_stats. */
+#define NLE_SCHED_AUTO 0
+#define NLE_SCHED_LEVEL 1
+#define NLE_SCHED_CHAIN 2
 
 /* BFGS update of the preconditioner (Section 3).  The full update uses
  * y_k = r_{k+1} - r_k; the paper's simplified update (eq. "lastprec", the
@@ -148,6 +175,10 @@ typedef struct {
   int ascending;                /* 1 when eigenvalues came out strictly ascending */
   double ms_batch;              /* device time of the batched launch that solved this
                                    problem (nle_batch_solve; 0 after nle_solve) */
+  int trsv_schedule;            /* NLE_SCHED_LEVEL or NLE_SCHED_CHAIN: the schedule in use */
+  double tune_ms_level;         /* autotuner: device ms of one (L L^T)^{-1} application with */
+  double tune_ms_chain;         /*   each schedule (0 when not timed) */
+  int64_t strands;              /* chain schedule: strands of L (runs of dependent rows) */
 } nle_stats;
 
 /* Parameters and outcome of one inner solve (nle_pcg). */
@@ -228,8 +259,10 @@ nle_status nle_backward(nle_t h, const double *gbar_lambda, const double *gbar_V
  * G = 4, or 8 when some handle was factored for more than 4 CTAs.
  * Requirements: every handle was factored for at most 8 CTAs (create it with
  * nle_options.grid_ctas = 4 or 8, or small enough n), all handles share the
- * precision and the device; the options of hs[0] apply and the work runs on
- * hs[0]'s stream.  p, tol, max_newton, max_pcg as in nle_solve.
+ * precision, the device and the schedule of the triangular solves (factor
+ * them with the same explicit nle_options.trsv_schedule; NLE_SCHED_AUTO may
+ * choose differently per matrix); the options of hs[0] apply and the work
+ * runs on hs[0]'s stream.  p, tol, max_newton, max_pcg as in nle_solve.
  * lambdas[b] [p] and Vs[b] [p*n_b] are device pointers; X0s may be NULL or
  * an array of device pointers (entries may be NULL: fixed pseudo-random
  * starts).  per_problem[b] (nullable) receives each problem's status; the

@@ -1,7 +1,7 @@
 """Build of the nle CUDA library (libnle.so) for sm_103a.
 
-The kernels are compiled once per (precision, rows-per-thread) pair in
-parallel translation units, then linked with the C ABI and the host set-up
+The kernels are compiled once per (precision, rows-per-thread, triangular-
+solve schedule) triple in parallel translation units, then linked with the C ABI and the host set-up
 code into ``paper_1312_1553_gb300/libnle.so``.  Objects go to ``_build/`` at
 the repository root.  A stamp over the sources and flags skips rebuilds.
 """
@@ -22,8 +22,9 @@ LIB = os.path.join(HERE, "libnle.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVFLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
            "--expt-relaxed-constexpr"] + ARCH
-VARIANTS = [("f1", "float", 1), ("f2", "float", 2), ("f4", "float", 4), ("f8", "float", 8),
-            ("d1", "double", 1), ("d2", "double", 2), ("d4", "double", 4), ("d8", "double", 8)]
+# (tag, precision, rows-per-thread chunks, chain schedule of the triangular solves)
+VARIANTS = [(f"{p}{r}{'c' if c else ''}", t, r, c) for c in (0, 1) for p, t in (("f", "float"), ("d", "double"))
+            for r in (1, 2, 4, 8)]
 
 
 def _nvcc() -> str:
@@ -60,9 +61,10 @@ def build(force: bool = False, jobs: int | None = None, verbose: bool = False) -
     cmds = []
     objs = []
     kern = os.path.join(CSRC, "nle_kernels.cu")
-    for tag, typ, rpc in VARIANTS:
+    for tag, typ, rpc, chain in VARIANTS:
         o = os.path.join(BUILD, f"nle_kernels_{tag}.o")
-        cmds.append([nvcc, *NVFLAGS, f"-DNLE_T={typ}", f"-DNLE_RPC={rpc}", f"-DNLE_TAG={tag}", "-c", kern, "-o", o])
+        cmds.append([nvcc, *NVFLAGS, f"-DNLE_T={typ}", f"-DNLE_RPC={rpc}", f"-DNLE_TAG={tag}",
+                     f"-DNLE_CHAIN_TU={chain}", "-c", kern, "-o", o])
         objs.append(o)
     for src in ("nle_api.cu", "nle_setup.cpp", "nle_noalloc.cu"):
         o = os.path.join(BUILD, src.replace(".", "_") + ".o")

@@ -17,35 +17,40 @@
 #include "nle_setup.h"
 
 namespace nle {
-// one translation unit of nle_kernels.cu per (precision, rows-per-thread)
-void *kernel_ptr_f1(int);
-void *kernel_ptr_f2(int);
-void *kernel_ptr_f4(int);
-void *kernel_ptr_f8(int);
-void *kernel_ptr_d1(int);
-void *kernel_ptr_d2(int);
-void *kernel_ptr_d4(int);
-void *kernel_ptr_d8(int);
+// one translation unit of nle_kernels.cu per (precision, rows-per-thread,
+// triangular-solve schedule)
+#define NLE_KTAB(tag) void *kernel_ptr_##tag(int);
+NLE_KTAB(f1) NLE_KTAB(f2) NLE_KTAB(f4) NLE_KTAB(f8) NLE_KTAB(d1) NLE_KTAB(d2) NLE_KTAB(d4) NLE_KTAB(d8)
+NLE_KTAB(f1c) NLE_KTAB(f2c) NLE_KTAB(f4c) NLE_KTAB(f8c) NLE_KTAB(d1c) NLE_KTAB(d2c) NLE_KTAB(d4c) NLE_KTAB(d8c)
+#undef NLE_KTAB
 enum KernelId { K_NEWTON = 0, K_DACG = 1, K_SHIFTED = 2, K_PREC = 3, K_PCG = 4, K_ADJOINT = 5, K_BATCH = 6 };
 template <typename T>
-void *kernel_ptr(int id, int rpc);
+void *kernel_ptr(int id, int rpc, int chain);
 template <>
-void *kernel_ptr<float>(int id, int rpc) {
-  switch (rpc) {
-    case 1: return kernel_ptr_f1(id);
-    case 2: return kernel_ptr_f2(id);
-    case 4: return kernel_ptr_f4(id);
-    case 8: return kernel_ptr_f8(id);
+void *kernel_ptr<float>(int id, int rpc, int chain) {
+  switch (rpc * 2 + (chain ? 1 : 0)) {
+    case 2: return kernel_ptr_f1(id);
+    case 3: return kernel_ptr_f1c(id);
+    case 4: return kernel_ptr_f2(id);
+    case 5: return kernel_ptr_f2c(id);
+    case 8: return kernel_ptr_f4(id);
+    case 9: return kernel_ptr_f4c(id);
+    case 16: return kernel_ptr_f8(id);
+    case 17: return kernel_ptr_f8c(id);
   }
   return nullptr;
 }
 template <>
-void *kernel_ptr<double>(int id, int rpc) {
-  switch (rpc) {
-    case 1: return kernel_ptr_d1(id);
-    case 2: return kernel_ptr_d2(id);
-    case 4: return kernel_ptr_d4(id);
-    case 8: return kernel_ptr_d8(id);
+void *kernel_ptr<double>(int id, int rpc, int chain) {
+  switch (rpc * 2 + (chain ? 1 : 0)) {
+    case 2: return kernel_ptr_d1(id);
+    case 3: return kernel_ptr_d1c(id);
+    case 4: return kernel_ptr_d2(id);
+    case 5: return kernel_ptr_d2c(id);
+    case 8: return kernel_ptr_d4(id);
+    case 9: return kernel_ptr_d4c(id);
+    case 16: return kernel_ptr_d8(id);
+    case 17: return kernel_ptr_d8c(id);
   }
   return nullptr;
 }
@@ -184,6 +189,12 @@ struct nle_ctx {
   DBuf d_perm, d_iperm;
   DBuf A_sptr, A_col, A_val, A64_val, d_diag;
   DBuf L_off, L_w, L_col, L_val, L_round, U_off, U_w, U_col, U_val, U_round;
+  DBuf L_wp, L_task, U_wp, U_task;  // chain schedule: per-warp task lists
+  DBuf L_hoff, L_hcol, U_hoff, U_hcol;  // level schedule: per-slab halo lists
+  int64_t hmax = 0;                      // longest halo list (0: no halo)
+  int chain = 0;                     // schedule of the triangular solves in use (1 = chain)
+  double tune_ms[2] = {0.0, 0.0};    // measured application time of the level / chain schedule
+  int64_t nstrands = 0;
   DBuf vecs;   // working-precision vectors
   DBuf vec64;  // Au, r, t
   DBuf dQ, dQt, dS, dR;
@@ -274,6 +285,18 @@ static Dev<T> make_dev(nle_t h) {
   D.Uval = h->U_val.as<T>();
   D.Uround = h->U_round.as<uint8_t>();
   D.rdiag = h->d_diag.as<T>();
+  D.chain = h->chain;
+  D.Lwp = h->L_wp.as<int32_t>();
+  D.Uwp = h->U_wp.as<int32_t>();
+  D.Ltask = h->L_task.as<int2>();
+  D.Utask = h->U_task.as<int2>();
+  D.hmax = h->hmax;
+  if (h->hmax > 0) {
+    D.Lhoff = h->L_hoff.as<int64_t>();
+    D.Uhoff = h->U_hoff.as<int64_t>();
+    D.Lhcol = h->L_hcol.as<int32_t>();
+    D.Uhcol = h->U_hcol.as<int32_t>();
+  }
   const int64_t np = h->npad, ext = h->npad + 32 * h->vw;
   T *v = h->vecs.as<T>();
   D.p = v + 0 * np;
@@ -316,6 +339,8 @@ static Opts make_opts(nle_t h, double tol, int max_newton, int max_pcg) {
   O.recompute = h->opt.dacg_recompute;
   O.spin_ns = (long long)(h->opt.spin_timeout_s * 1e9);
   O.trsv_warps = h->opt.trsv_warps;
+  O.halo_k = std::max(1, std::min(8, h->opt.halo_window));
+  O.halo_sleep_ns = std::max(0, h->opt.halo_backoff_ns);
   O.bfgs_full = h->opt.bfgs_update == NLE_BFGS_FULL ? 1 : 0;
   return O;
 }
@@ -323,10 +348,11 @@ static Opts make_opts(nle_t h, double tol, int max_newton, int max_pcg) {
 // Cooperative launch of kernel `id` (persistent, gridDim = h->grid).
 template <typename T>
 static nle_status launch(nle_t h, int id, void **args) {
-  void *fn = kernel_ptr<T>(id, h->rpc);
+  void *fn = kernel_ptr<T>(id, h->rpc, h->chain);
   if (!fn) return fail(h, NLE_ERR_ARG, "no kernel instance for this size");
   // dynamic shared memory: two slab-sized buffers of the triangular solves
-  const size_t dyn = 2 * (size_t)h->bsize * (mixed(h) ? 4 : 8);
+  // and the halo buffer
+  const size_t dyn = (2 * (size_t)h->bsize + (size_t)h->hmax) * (mixed(h) ? 4 : 8);
   NLE_CUDA(h, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
   int nb = 0;
   NLE_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, TPB, dyn));
@@ -389,6 +415,134 @@ static nle_status get_vector(nle_t h, const T *src, double *dst, int on_device) 
   return NLE_OK;
 }
 
+// Device layout of a factored handle: the relabelling, A in SELL (working
+// precision and FP64), the triangular factors in the layout of the chosen
+// schedule (chain = 1: the factored matrix's own order with per-warp task
+// lists; 0: slab-major level-minor order with level rounds), uploaded on the
+// handle's stream.  rp/ci/va: the matrix that was factored.
+template <typename TV>
+static nle_status upload_layout(nle_t h, const Permuted &P, bool level_rounds, int chain) {
+  const int H = 32 * h->vw;
+  SellSet<TV> S;
+  build_sell<TV>(P, H, h->bsize, level_rounds, S);
+  NLE_CUDA(h, upload(h->A_sptr, S.A.sptr, h->stream));
+  NLE_CUDA(h, upload(h->A_col, S.A.col, h->stream));
+  NLE_CUDA(h, upload(h->A_val, S.A.val, h->stream));
+  NLE_CUDA(h, upload(h->A64_val, S.A64.val, h->stream));
+  NLE_CUDA(h, upload(h->d_diag, S.diag, h->stream));
+  if (chain) {
+    const int nw = std::max(1, std::min(NWARP, h->opt.trsv_warps));
+    ChainHost<TV> CL, CU;
+    build_chain<TV>(P, h->bsize, true, nw, CL);
+    build_chain<TV>(P, h->bsize, false, nw, CU);
+    h->nstrands = CL.nstrands;
+    S.L = std::move(CL.ell);
+    S.U = std::move(CU.ell);
+    NLE_CUDA(h, upload(h->L_wp, CL.wptr, h->stream));
+    NLE_CUDA(h, upload(h->L_task, CL.task, h->stream));
+    NLE_CUDA(h, upload(h->U_wp, CU.wptr, h->stream));
+    NLE_CUDA(h, upload(h->U_task, CU.task, h->stream));
+    S.L.round.assign(1, 0);
+    S.U.round.assign(1, 0);
+  }
+  h->hmax = 0;
+  if (!chain && !level_rounds && h->opt.trsv_halo) {
+    // halo lists when they fit in shared memory beside the two slab buffers
+    const int64_t limit = (int64_t)(192 * 1024 / sizeof(TV)) - 2 * h->bsize;
+    std::vector<int64_t> lo, uo;
+    std::vector<int32_t> lc, uc;
+    const int64_t hl = build_halo<TV>(S.L, h->npad, h->bsize, true, limit, P.lev, h->opt.trsv_halo, lo, lc);
+    if (hl >= 0) {
+      const int64_t hu = build_halo<TV>(S.U, h->npad, h->bsize, false, limit, P.levU, h->opt.trsv_halo, uo, uc);
+      if (hu < 0) {
+        // undo L's remapping: rebuild its ELL
+        build_sell<TV>(P, H, h->bsize, level_rounds, S);
+      } else {
+        h->hmax = std::max<int64_t>(1, std::max(hl, hu));
+        NLE_CUDA(h, upload(h->L_hoff, lo, h->stream));
+        NLE_CUDA(h, upload(h->L_hcol, lc, h->stream));
+        NLE_CUDA(h, upload(h->U_hoff, uo, h->stream));
+        NLE_CUDA(h, upload(h->U_hcol, uc, h->stream));
+      }
+    }
+  }
+  NLE_CUDA(h, upload(h->L_off, S.L.off, h->stream));
+  NLE_CUDA(h, upload(h->L_w, S.L.width, h->stream));
+  NLE_CUDA(h, upload(h->L_col, S.L.col, h->stream));
+  NLE_CUDA(h, upload(h->L_val, S.L.val, h->stream));
+  NLE_CUDA(h, upload(h->L_round, S.L.round, h->stream));
+  NLE_CUDA(h, upload(h->U_off, S.U.off, h->stream));
+  NLE_CUDA(h, upload(h->U_w, S.U.width, h->stream));
+  NLE_CUDA(h, upload(h->U_col, S.U.col, h->stream));
+  NLE_CUDA(h, upload(h->U_val, S.U.val, h->stream));
+  NLE_CUDA(h, upload(h->U_round, S.U.round, h->stream));
+  // the host vectors above are released on return: copies from pageable
+  // memory are staged before cudaMemcpyAsync returns
+  return NLE_OK;
+}
+
+static nle_status build_layout(nle_t h, const std::vector<int32_t> &P0, const int64_t *rp, const int32_t *ci,
+                               const double *va, int chain) {
+  if (chain) {
+    h->perm.resize(h->n);
+    h->iperm.resize(h->n);
+    for (int64_t i = 0; i < h->n; i++) h->perm[i] = h->iperm[i] = (int32_t)i;
+  } else {
+    // with a multicolour ordering the slabs still follow the caller's row
+    // order (P0[k] = caller's row of row k of P A P^T), which keeps each
+    // slab's rows and their neighbours together
+    slab_level_order(h->F, h->bsize, P0.empty() ? nullptr : P0.data(), h->perm, h->iperm);
+  }
+  Permuted P;
+  permute(h->n, rp, ci, va, h->F, h->perm, h->iperm, h->npad, P);
+  if (!P0.empty()) {
+    // device position -> row of the caller's numbering, through P A P^T
+    for (int64_t p = 0; p < h->n; p++) h->perm[p] = P0[h->perm[p]];
+    for (int64_t p = 0; p < h->n; p++) h->iperm[h->perm[p]] = (int32_t)p;
+  }
+  nle_status s = mixed(h) ? upload_layout<float>(h, P, !P0.empty(), chain)
+                          : upload_layout<double>(h, P, !P0.empty(), chain);
+  if (s != NLE_OK) return s;
+  NLE_CUDA(h, upload(h->d_perm, h->perm, h->stream));
+  NLE_CUDA(h, upload(h->d_iperm, h->iperm, h->stream));
+  h->chain = chain;
+  return NLE_OK;
+}
+
+// Device time of one application of (L L^T)^{-1} (k = 0 pairs, no
+// projection) with the handle's current layout: the median of three
+// launches after one warm-up, on the handle's stream.
+template <typename T>
+static nle_status time_precond_t(nle_t h, double *ms) {
+  Dev<T> D = make_dev<T>(h);
+  k_default_start<<<1024, 256, 0, h->stream>>>(h->scratch.as<double>(), h->n, 0);
+  NLE_CUDA(h, cudaGetLastError());
+  k_gather<T><<<1024, 256, 0, h->stream>>>(D.g, h->scratch.as<double>(), h->d_perm.as<int32_t>(), h->n, h->npad);
+  NLE_CUDA(h, cudaGetLastError());
+  Opts O = make_opts(h, 1e-8, 1, 1);
+  NLE_CUDA(h, cudaMemsetAsync(h->state.p, 0, sizeof(State), h->stream));
+  int m = 0, k = 0;
+  void *args[] = {&D, &O, &m, &k};
+  float t[4];
+  for (int it = 0; it < 4; it++) {
+    NLE_CUDA(h, cudaEventRecord(h->ev[0], h->stream));
+    nle_status s = launch<T>(h, K_PREC, args);
+    if (s != NLE_OK) return s;
+    NLE_CUDA(h, cudaEventRecord(h->ev[1], h->stream));
+    NLE_CUDA(h, cudaEventSynchronize(h->ev[1]));
+    NLE_CUDA(h, cudaEventElapsedTime(&t[it], h->ev[0], h->ev[1]));
+  }
+  nle_status s = check_state_error(h);
+  if (s != NLE_OK) return s;
+  std::sort(t + 1, t + 4);
+  *ms = t[2];
+  return NLE_OK;
+}
+
+static nle_status time_precond(nle_t h, double *ms) {
+  return mixed(h) ? time_precond_t<float>(h, ms) : time_precond_t<double>(h, ms);
+}
+
 // ---------------------------------------------------------------------------
 // C ABI
 // ---------------------------------------------------------------------------
@@ -409,6 +563,10 @@ void nle_default_options(nle_options *o) {
   o->trsv_warps = 16;
   o->ordering = NLE_ORDER_NATURAL;
   o->bfgs_update = NLE_BFGS_SIMPLIFIED;
+  o->trsv_schedule = NLE_SCHED_AUTO;
+  o->trsv_halo = 0;
+  o->halo_window = 4;
+  o->halo_backoff_ns = 0;
 }
 
 const char *nle_last_error(nle_t h) { return h ? h->err.c_str() : g_create_error.c_str(); }
@@ -439,6 +597,8 @@ nle_status nle_create(int64_t n, int64_t nnz, const int64_t *rowptr, const int32
   if (h->opt.trsv_warps < 1 || h->opt.trsv_warps > NWARP) return fail(nullptr, NLE_ERR_ARG, "trsv_warps out of range");
   if (h->opt.ordering < NLE_ORDER_NATURAL || h->opt.ordering > NLE_ORDER_MULTICOLOR2)
     return fail(nullptr, NLE_ERR_ARG, "unknown ordering");
+  if (h->opt.trsv_schedule < NLE_SCHED_AUTO || h->opt.trsv_schedule > NLE_SCHED_CHAIN)
+    return fail(nullptr, NLE_ERR_ARG, "unknown trsv_schedule");
   if (h->opt.bfgs_update != NLE_BFGS_SIMPLIFIED && h->opt.bfgs_update != NLE_BFGS_FULL)
     return fail(nullptr, NLE_ERR_ARG, "unknown bfgs_update");
   if (h->opt.bfgs_update == NLE_BFGS_FULL && h->opt.k_max > NLE_MAX_KMAX - 1)
@@ -552,57 +712,7 @@ nle_status nle_factor_ic(nle_t h, int lfil, double tau_ic) {
   h->bsize = ((h->npad + TRSV_ROWS * grid - 1) / (TRSV_ROWS * grid)) * TRSV_ROWS;
   if (2 * h->bsize * (int64_t)(mixed(h) ? 4 : 8) > 192 * 1024)
     return fail(h, NLE_ERR_ARG, "n too large for the shared-memory slab of one persistent grid");
-  // with a multicolour ordering the slabs still follow the caller's row
-  // order (P0[k] = caller's row of row k of P A P^T), which keeps each
-  // slab's rows and their neighbours together
-  slab_level_order(h->F, h->bsize, P0.empty() ? nullptr : P0.data(), h->perm, h->iperm);
-  Permuted P;
-  permute(h->n, rp, ci, va, h->F, h->perm, h->iperm, h->npad, P);
-  if (!P0.empty()) {
-    // device position -> row of the caller's numbering, through P A P^T
-    for (int64_t p = 0; p < h->n; p++) h->perm[p] = P0[h->perm[p]];
-    for (int64_t p = 0; p < h->n; p++) h->iperm[h->perm[p]] = (int32_t)p;
-  }
   const size_t tsz = mixed(h) ? 4 : 8;
-  if (mixed(h)) {
-    SellSet<float> S;
-    build_sell<float>(P, H, h->bsize, !P0.empty(), S);
-    NLE_CUDA(h, upload(h->A_sptr, S.A.sptr, h->stream));
-    NLE_CUDA(h, upload(h->A_col, S.A.col, h->stream));
-    NLE_CUDA(h, upload(h->A_val, S.A.val, h->stream));
-    NLE_CUDA(h, upload(h->A64_val, S.A64.val, h->stream));
-    NLE_CUDA(h, upload(h->L_off, S.L.off, h->stream));
-    NLE_CUDA(h, upload(h->L_w, S.L.width, h->stream));
-    NLE_CUDA(h, upload(h->L_col, S.L.col, h->stream));
-    NLE_CUDA(h, upload(h->L_val, S.L.val, h->stream));
-    NLE_CUDA(h, upload(h->L_round, S.L.round, h->stream));
-    NLE_CUDA(h, upload(h->U_off, S.U.off, h->stream));
-    NLE_CUDA(h, upload(h->U_w, S.U.width, h->stream));
-    NLE_CUDA(h, upload(h->U_col, S.U.col, h->stream));
-    NLE_CUDA(h, upload(h->U_val, S.U.val, h->stream));
-    NLE_CUDA(h, upload(h->U_round, S.U.round, h->stream));
-    NLE_CUDA(h, upload(h->d_diag, S.diag, h->stream));
-  } else {
-    SellSet<double> S;
-    build_sell<double>(P, H, h->bsize, !P0.empty(), S);
-    NLE_CUDA(h, upload(h->A_sptr, S.A.sptr, h->stream));
-    NLE_CUDA(h, upload(h->A_col, S.A.col, h->stream));
-    NLE_CUDA(h, upload(h->A_val, S.A.val, h->stream));
-    NLE_CUDA(h, upload(h->A64_val, S.A64.val, h->stream));
-    NLE_CUDA(h, upload(h->L_off, S.L.off, h->stream));
-    NLE_CUDA(h, upload(h->L_w, S.L.width, h->stream));
-    NLE_CUDA(h, upload(h->L_col, S.L.col, h->stream));
-    NLE_CUDA(h, upload(h->L_val, S.L.val, h->stream));
-    NLE_CUDA(h, upload(h->L_round, S.L.round, h->stream));
-    NLE_CUDA(h, upload(h->U_off, S.U.off, h->stream));
-    NLE_CUDA(h, upload(h->U_w, S.U.width, h->stream));
-    NLE_CUDA(h, upload(h->U_col, S.U.col, h->stream));
-    NLE_CUDA(h, upload(h->U_val, S.U.val, h->stream));
-    NLE_CUDA(h, upload(h->U_round, S.U.round, h->stream));
-    NLE_CUDA(h, upload(h->d_diag, S.diag, h->stream));
-  }
-  NLE_CUDA(h, upload(h->d_perm, h->perm, h->stream));
-  NLE_CUDA(h, upload(h->d_iperm, h->iperm, h->stream));
   const int64_t ext = h->npad + 32 * h->vw;
   NLE_CUDA(h, dalloc(h->vecs, (size_t)(8 * h->npad + 2 * ext) * tsz, h->stream));
   NLE_CUDA(h, dalloc(h->vec64, (size_t)5 * h->npad * 8, h->stream));
@@ -614,6 +724,25 @@ nle_status nle_factor_ic(nle_t h, int lfil, double tau_ic) {
   h->ldq = 0;
   nle_status s = ensure_q(h, 8);
   if (s != NLE_OK) return s;
+  // schedule of the triangular solves: the chain schedule needs the factored
+  // matrix's own row order (natural ordering); NLE_SCHED_AUTO times one
+  // preconditioner application with each schedule and keeps the faster
+  const bool chain_ok = P0.empty();
+  int sched = h->opt.trsv_schedule;
+  if (sched == NLE_SCHED_CHAIN && !chain_ok)
+    return fail(h, NLE_ERR_ARG, "the chain schedule needs the natural ordering");
+  h->tune_ms[0] = h->tune_ms[1] = 0.0;
+  if (sched == NLE_SCHED_AUTO && chain_ok) {
+    for (int c = 0; c < 2; c++) {
+      if ((s = build_layout(h, P0, rp, ci, va, c)) != NLE_OK) return s;
+      if ((s = time_precond(h, &h->tune_ms[c])) != NLE_OK) return s;
+    }
+    // the chain layout is in place; go back to the level layout if it was faster
+    sched = h->tune_ms[1] < h->tune_ms[0] ? NLE_SCHED_CHAIN : NLE_SCHED_LEVEL;
+    if (sched == NLE_SCHED_LEVEL && (s = build_layout(h, P0, rp, ci, va, 0)) != NLE_OK) return s;
+  } else {
+    if ((s = build_layout(h, P0, rp, ci, va, sched == NLE_SCHED_CHAIN ? 1 : 0)) != NLE_OK) return s;
+  }
   NLE_CUDA(h, cudaStreamSynchronize(h->stream));
   h->factored = true;
   return NLE_OK;
@@ -668,6 +797,14 @@ static void fill_stats(const State &st, int p, double ms_dacg, double ms_newton,
   for (int q = 0; q < 8; q++) stats->ms_phase[q] = st.tphase[q] * 1e-6;
   stats->ascending = asc ? 1 : 0;
   stats->ms_batch = ms_batch;
+}
+
+// schedule of the handle's triangular solves and the autotuner's timings
+static void schedule_stats(nle_t h, nle_stats *stats) {
+  stats->trsv_schedule = h->chain ? NLE_SCHED_CHAIN : NLE_SCHED_LEVEL;
+  stats->tune_ms_level = h->tune_ms[0];
+  stats->tune_ms_chain = h->tune_ms[1];
+  stats->strands = h->chain ? h->nstrands : 0;
 }
 
 template <typename T>
@@ -734,6 +871,7 @@ static nle_status solve_impl(nle_t h, int p, double tol, int max_newton, int max
   bool allconv = true;
   for (int j = 0; j < p; j++) allconv = allconv && st.conv[j];
   fill_stats(st, p, ms_dacg, ms_newton, launches, 0.0, &h->last_stats);
+  schedule_stats(h, &h->last_stats);
   h->has_stats = true;
   if (stats) *stats = h->last_stats;
   if (!allconv) return fail(h, NLE_ERR_NOCONV, "some eigenpairs reached max_newton");
@@ -766,7 +904,7 @@ static nle_status shifted_impl(nle_t h, double theta, const double *x, double *y
   Dev<T> D = make_dev<T>(h);
   nle_status s = put_vectors<T>(h, x, 1, D.p, on_dev);
   if (s != NLE_OK) return s;
-  void *fn = kernel_ptr<T>(K_SHIFTED, h->rpc);
+  void *fn = kernel_ptr<T>(K_SHIFTED, h->rpc, h->chain);
   void *args[] = {&D, &theta};
   NLE_CUDA(h, cudaLaunchKernel(fn, dim3(h->grid), dim3(TPB), args, 0, h->stream));
   s = get_vector<T>(h, D.y, y, on_dev);
@@ -971,7 +1109,7 @@ static nle_status batch_impl(int count, nle_t *hs, int p, double tol, int max_ne
     NLE_CUDA(h0, cudaMemsetAsync(h->state.p, 0, sizeof(State), h->stream));
     NLE_CUDA(h0, cudaStreamSynchronize(h->stream));
     while ((int64_t)rpc * h->grid * TPB < h->nchunks) rpc *= 2;
-    dyn = std::max(dyn, 2 * (size_t)h->bsize * sizeof(T));
+    dyn = std::max(dyn, (2 * (size_t)h->bsize + (size_t)h->hmax) * sizeof(T));
     order[b] = b;
   }
   if (rpc > 8) return fail(h0, NLE_ERR_ARG, "a problem is too large for its CTA group");
@@ -997,7 +1135,7 @@ static nle_status batch_impl(int count, nle_t *hs, int p, double tol, int max_ne
   // phases), at least the barrier limit itself
   B.group_spin_ns = (long long)(h0->opt.spin_timeout_s * 1e9 * 64.0 * p);
   Opts O = make_opts(h0, tol, max_newton, max_pcg);
-  void *fn = kernel_ptr<T>(K_BATCH, rpc);
+  void *fn = kernel_ptr<T>(K_BATCH, rpc, h0->chain);
   if (!fn) return fail(h0, NLE_ERR_ARG, "no kernel instance for this size");
   NLE_CUDA(h0, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
   int nb = 0;
@@ -1036,6 +1174,7 @@ static nle_status batch_impl(int count, nle_t *hs, int p, double tol, int max_ne
       h->solved = true;
     }
     fill_stats(st, p, 0.0, 0.0, 0, ms, &h->last_stats);
+    schedule_stats(h, &h->last_stats);
     h->has_stats = true;
     if (per_problem) per_problem[b] = s;
     if (s != NLE_OK && (worst == NLE_OK || worst == NLE_ERR_NOCONV)) worst = s;
@@ -1053,6 +1192,9 @@ extern "C" nle_status nle_batch_solve(int count, nle_t *hs, int p, double tol, i
     if (!hs[b]->factored) return fail(hs[b], NLE_ERR_STATE, "nle_factor_ic has not been called");
     if (hs[b]->opt.precision != hs[0]->opt.precision || hs[b]->device != hs[0]->device)
       return fail(hs[b], NLE_ERR_ARG, "all handles of a batch need the same precision and device");
+    if (hs[b]->chain != hs[0]->chain)
+      return fail(hs[b], NLE_ERR_ARG,
+                  "all handles of a batch need the same triangular-solve schedule (set nle_options.trsv_schedule)");
     if (hs[b]->grid > 8)
       return fail(hs[b], NLE_ERR_ARG, "batched handles must be factored for at most 8 CTAs (nle_options.grid_ctas <= 8)");
     if (p < 1 || p >= hs[b]->n || p > NLE_MAX_P || !lambdas[b] || !Vs[b])

@@ -167,6 +167,7 @@ struct Ctl {
   int rbuf;        // reduction buffer parity
   long long spin_ns;
   int twarps;      // warps of this CTA that take part in the triangular solves
+  int halo_k, halo_sleep_ns;
 };
 
 // Phase timers: CTA 0 / thread 0 charges the time since the last mark to
@@ -388,11 +389,26 @@ __device__ __forceinline__ void trsv_fetch(const TriEll<T> &M, int64_t b0, int64
   }
 }
 
-// Current value of dependency c: the shared copy inside the slab, global
-// memory outside it (the not-yet-computed marker if it is not ready).
+// Where a triangular solve reads its dependencies: its CTA's slab [b0, b1)
+// of the output x is copied in shared memory (stage); a dependency in
+// another slab is either read from global memory or, when the factor's
+// entries were remapped to a halo (column = TRSV_HALO + slot), from the
+// CTA's shared-memory halo buffer, which its copy warp fills.
 template <typename T>
-__device__ __forceinline__ T trsv_peek(const T *x, const volatile T *stage, int64_t b0, int64_t b1, int c) {
-  return (c >= b0 && c < b1) ? stage[c - b0] : ld_relaxed(x + c);
+struct TriSrc {
+  const T *x;
+  const volatile T *stage;
+  const volatile T *halo;
+  int64_t b0, b1;
+};
+
+// Current value of dependency c (the not-yet-computed marker if it is not
+// ready).
+template <typename T>
+__device__ __forceinline__ T trsv_peek(const TriSrc<T> &S, int c) {
+  if (c >= S.b0 && c < S.b1) return S.stage[c - S.b0];
+  if (c >= TRSV_HALO) return S.halo[c - TRSV_HALO];
+  return ld_relaxed(S.x + c);
 }
 
 // Warp-uniform wait: returns once every lane of the warp holds values (not
@@ -400,8 +416,7 @@ __device__ __forceinline__ T trsv_peek(const T *x, const volatile T *stage, int6
 // only after 2^20 rounds of polling; past spin_ns the wait records
 // NLE_ERR_TIMEOUT and substitutes 0 so that dependants still finish.
 template <int N, typename T>
-__device__ __forceinline__ void trsv_wait(const T *x, const volatile T *stage, int64_t b0, int64_t b1, const int *c,
-                                          T *v, State *st, long long spin_ns) {
+__device__ __forceinline__ void trsv_wait(const TriSrc<T> &S, const int *c, T *v, State *st, long long spin_ns) {
   auto ready = [&]() {
     bool ok = true;
 #pragma unroll
@@ -414,7 +429,7 @@ __device__ __forceinline__ void trsv_wait(const T *x, const volatile T *stage, i
   for (int it = 0;; it++) {
 #pragma unroll
     for (int k = 0; k < N; k++)
-      if (c[k] >= 0 && is_sent(v[k])) v[k] = trsv_peek(x, stage, b0, b1, c[k]);
+      if (c[k] >= 0 && is_sent(v[k])) v[k] = trsv_peek(S, c[k]);
     ok = ready();
     if (__all_sync(0xffffffffu, ok)) return;
     if (it >= (1 << 20)) {
@@ -431,17 +446,101 @@ __device__ __forceinline__ void trsv_wait(const T *x, const volatile T *stage, i
   }
 }
 
+// Copy warp of the halo: lane l moves halo entries l, l + 32, ... (in the
+// order the slab first needs them) from global memory into shared memory as
+// their producers publish them, HALO_K loads in flight per lane, so that
+// the solving warps never wait on a global-memory round trip for a value
+// that is already there.  Its waits end because every halo value comes from
+// a slab that does not depend on this one (lower slabs for L, higher for
+// L^T); they are also bounded in time (reset by every completed entry),
+// after which the remaining entries are set to 0 and NLE_ERR_TIMEOUT is
+// recorded.
+constexpr int HALO_K = 8;
+
+template <typename T>
+__device__ __forceinline__ void halo_copy(const T *x, volatile T *halo, const int32_t *hcol, int hcnt, State *st,
+                                          long long spin_ns, int K, int sleep_ns) {
+  const int lane = threadIdx.x & 31;
+  int idx[HALO_K];
+  T v[HALO_K];
+  int nxt = lane;
+#pragma unroll
+  for (int k = 0; k < HALO_K; k++) {
+    idx[k] = -1;
+    v[k] = T(0);
+    if (k < K && nxt < hcnt) {
+      idx[k] = nxt;
+      v[k] = ld_relaxed(x + __ldg(hcol + nxt));
+      nxt += 32;
+    }
+  }
+  long long t0 = 0;
+  int spins = 0;
+  for (;;) {
+    bool any = false, moved = false;
+#pragma unroll
+    for (int k = 0; k < HALO_K; k++) {
+      if (idx[k] < 0) continue;
+      if (!is_sent(v[k])) {
+        halo[idx[k]] = v[k];
+        moved = true;
+        idx[k] = -1;
+        if (nxt < hcnt) {
+          idx[k] = nxt;
+          v[k] = ld_relaxed(x + __ldg(hcol + nxt));
+          nxt += 32;
+        }
+      } else {
+        v[k] = ld_relaxed(x + __ldg(hcol + idx[k]));
+      }
+      any = any || idx[k] >= 0;
+    }
+    if (!any) break;
+    if (!moved && sleep_ns > 0) __nanosleep(sleep_ns);
+    if (moved) {
+      t0 = 0;
+      spins = 0;
+    } else if (++spins >= 64) {
+      spins = 0;
+      const long long now = gtimer();
+      if (t0 == 0) {
+        t0 = now;
+      } else if (now - t0 > spin_ns) {
+        record_error(st, 8 /*NLE_ERR_TIMEOUT*/, 103);
+#pragma unroll
+        for (int k = 0; k < HALO_K; k++)
+          if (idx[k] >= 0) halo[idx[k]] = T(0);
+        for (; nxt < hcnt; nxt += 32) halo[nxt] = T(0);
+        break;
+      }
+    }
+  }
+}
+
 template <bool LOWER, typename T, typename RHS>
 __device__ __forceinline__ void trsv_block(const TriEll<T> &M, T *x, int64_t npad, int64_t bsize, int twarps,
-                                           long long spin_ns, State *st, T *stage_mem, RHS rhs_of) {
+                                           long long spin_ns, State *st, T *stage_mem, T *halo_mem,
+                                           const int64_t *hoff, const int32_t *hcol, int halo_k, int halo_sleep_ns,
+                                           RHS rhs_of) {
   const int64_t b0 = (int64_t)grank() * bsize;
   const int64_t b1 = min(npad, b0 + bsize);
   const int64_t nb = b1 > b0 ? b1 - b0 : 0;
   volatile T *stage = stage_mem;
+  volatile T *halo = halo_mem;
   const T sent = sentinel<T>();
   for (int64_t i = threadIdx.x; i < nb; i += blockDim.x) stage[i] = sent;
+  // halo mode: the last warp copies the slab's halo, the others solve
+  int64_t h0 = 0, hcnt = 0;
+  if (hcol && nb > 0) {
+    h0 = __ldg(hoff + grank());
+    hcnt = __ldg(hoff + grank() + 1) - h0;
+    twarps = min(twarps, NWARP - 1);
+    for (int64_t i = threadIdx.x; i < hcnt; i += blockDim.x) halo[i] = sent;
+  }
   __syncthreads();
+  const TriSrc<T> S{x, stage, halo, b0, b1};
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (hcnt > 0 && warp == NWARP - 1) halo_copy<T>(x, halo, hcol + h0, (int)hcnt, st, spin_ns, halo_k, halo_sleep_ns);
   const int64_t ngrp = nb / TRSV_ROWS;
   int64_t it = warp;
   if (warp < twarps && it < ngrp) {
@@ -462,9 +561,9 @@ __device__ __forceinline__ void trsv_block(const TriEll<T> &M, T *x, int64_t npa
         for (int k = 0; k < TRSV_EPL; k++) {
           c[k] = active ? cur.c[k] : -1;
           v[k] = T(0);
-          if (c[k] >= 0) v[k] = trsv_peek(x, stage, b0, b1, c[k]);
+          if (c[k] >= 0) v[k] = trsv_peek(S, c[k]);
         }
-        trsv_wait<TRSV_EPL, T>(x, stage, b0, b1, c, v, st, spin_ns);
+        trsv_wait<TRSV_EPL, T>(S, c, v, st, spin_ns);
         T acc = T(0);
 #pragma unroll
         for (int k = 0; k < TRSV_EPL; k++)
@@ -475,8 +574,8 @@ __device__ __forceinline__ void trsv_block(const TriEll<T> &M, T *x, int64_t npa
         for (int k = g + 16; k < wd; k += TRSV_LANES) {
           int ce[1] = {active ? __ldg(M.col + e + k) : -1};
           T ve[1] = {T(0)};
-          if (ce[0] >= 0) ve[0] = trsv_peek(x, stage, b0, b1, ce[0]);
-          trsv_wait<1, T>(x, stage, b0, b1, ce, ve, st, spin_ns);
+          if (ce[0] >= 0) ve[0] = trsv_peek(S, ce[0]);
+          trsv_wait<1, T>(S, ce, ve, st, spin_ns);
           if (ce[0] >= 0) acc += __ldg(M.val + e + k) * ve[0];
         }
 #pragma unroll
@@ -503,6 +602,174 @@ __device__ __forceinline__ void trsv_block(const TriEll<T> &M, T *x, int64_t npa
       process(p1, it1);
       if (it2 >= ngrp) break;
       it = it2;
+    }
+  }
+  __syncthreads();
+}
+
+// Chain schedule of the sync-free triangular solve, one slab per CTA.
+//
+// The slab's rows (the factored matrix's own order) are cut into tasks of at
+// most TRSV_ROWS consecutive rows in processing order (ascending for L,
+// descending for L^T), and every warp owns a list of tasks, built on the
+// host: runs of tasks whose first row depends on the previous task's last
+// row ("strands", the lines of a grid in natural order) stay on one warp.
+// A task is solved with TRSV_LANES lanes per row: the entries pointing to
+// rows outside the task and outside the previous task's last row are
+// "external" and gathered as in trsv_block (shared-memory copy inside the
+// slab, relaxed global loads outside it, the value being its own ready
+// flag, bounded warp-uniform wait); the entries pointing to earlier rows of
+// the same task or to the previous task's last row are stored with column
+// -2 - d (d = distance back in processing order) and resolved in registers,
+// so a dependency chain along a strand costs one shuffle per row instead
+// of a trip through memory:
+//   v_a = rhs_a - sum_external L_ac x_c - L_{a,prev} x_prev,
+//   x_s = v_s / L_ss and v_a -= L_as x_s for a > s, s = 0, 1, ...
+// The next task's entries are fetched, and its external values loaded,
+// before the current task waits, which hides the latency of the loads from
+// other slabs behind the current task.  Every wait ends: the host deals the
+// strands to the warps in a topological order of the strand graph of each
+// slab and every dependency points to a lower slab (L) or a higher one
+// (L^T), so the earliest unfinished task always has its inputs; all CTAs
+// are resident (cooperative launch) and every wait is also bounded in time.
+template <typename T>
+struct TriChain {
+  const int64_t *off;    // per slab: first entry
+  const int32_t *width;  // per slab: entries per row (multiple of 8)
+  const int32_t *col;    // -1 = padding, -2 - d = register-resolved entry
+  const T *val;
+  const T *rdiag;
+  const int32_t *wptr;   // per slab: NWARP + 1 offsets into task
+  const int2 *task;      // {first row processed, rows | sequential << 3}
+};
+
+template <typename T>
+struct ChainPre {
+  int c[TRSV_EPL];
+  T a[TRSV_EPL];
+  T v[TRSV_EPL];  // values of the external entries (loaded ahead; marker if not ready)
+  T rhs, rdg;
+  int r0, meta;
+};
+
+template <bool LOWER, typename T, typename RHS>
+__device__ __forceinline__ void chain_fetch(const TriChain<T> &M, const TriSrc<T> &S, int64_t b0, int64_t base, int wd,
+                                            int ti, int q, int g, RHS &rhs_of, ChainPre<T> &P) {
+  const int2 tk = __ldg(M.task + ti);
+  P.r0 = tk.x;
+  P.meta = tk.y;
+  const bool active = q < (tk.y & 7);
+  const int64_t r = LOWER ? (int64_t)tk.x + q : (int64_t)tk.x - q;
+  const int64_t e = base + (r - b0) * wd + g;
+#pragma unroll
+  for (int k = 0; k < TRSV_EPL; k++) {
+    P.c[k] = -1;
+    P.a[k] = T(0);
+    if (active && g + k * TRSV_LANES < wd) {
+      P.c[k] = __ldg(M.col + e + k * TRSV_LANES);
+      P.a[k] = __ldg(M.val + e + k * TRSV_LANES);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < TRSV_EPL; k++) P.v[k] = (P.c[k] >= 0) ? trsv_peek(S, P.c[k]) : T(0);
+  P.rhs = T(0);
+  P.rdg = T(1);
+  if (active) {
+    P.rhs = rhs_of(r);
+    P.rdg = __ldg(M.rdiag + r);
+  }
+}
+
+template <bool LOWER, typename T, typename RHS>
+__device__ __forceinline__ void trsv_chain(const TriChain<T> &M, T *x, int64_t npad, int64_t bsize, long long spin_ns,
+                                           State *st, T *stage_mem, RHS rhs_of) {
+  const int64_t b0 = (int64_t)grank() * bsize;
+  const int64_t b1 = min(npad, b0 + bsize);
+  const int64_t nb = b1 > b0 ? b1 - b0 : 0;
+  volatile T *stage = stage_mem;
+  const T sent = sentinel<T>();
+  for (int64_t i = threadIdx.x; i < nb; i += blockDim.x) stage[i] = sent;
+  __syncthreads();
+  const TriSrc<T> S{x, stage, nullptr, b0, b1};
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // a CTA past the last slab has no rows (and no task offsets)
+  const int t0 = nb > 0 ? __ldg(M.wptr + grank() * (NWARP + 1) + warp) : 0;
+  const int t1 = nb > 0 ? __ldg(M.wptr + grank() * (NWARP + 1) + warp + 1) : 0;
+  if (t0 < t1) {
+    const int q = lane / TRSV_LANES, g = lane % TRSV_LANES;
+    const int64_t base = __ldg(M.off + grank());
+    const int wd = __ldg(M.width + grank());
+    T xprev = T(0);
+    auto process = [&](ChainPre<T> &cur) {
+      const int cnt = cur.meta & 7;
+      const int64_t r = LOWER ? (int64_t)cur.r0 + q : (int64_t)cur.r0 - q;
+      const bool active = q < cnt;
+      trsv_wait<TRSV_EPL, T>(S, cur.c, cur.v, st, spin_ns);
+      T acc = T(0), cf[TRSV_ROWS];
+#pragma unroll
+      for (int d = 0; d < TRSV_ROWS; d++) cf[d] = T(0);
+#pragma unroll
+      for (int k = 0; k < TRSV_EPL; k++) {
+        if (cur.c[k] >= 0) acc += cur.a[k] * cur.v[k];
+#pragma unroll
+        for (int d = 0; d < TRSV_ROWS; d++)
+          if (cur.c[k] == -3 - d) cf[d] += cur.a[k];
+      }
+      // external entries beyond the first 16 of a row (same trip count in
+      // every lane)
+      const int64_t e = base + (r - b0) * wd;
+      for (int k = g + 16; k < wd; k += TRSV_LANES) {
+        int ce[1] = {active ? __ldg(M.col + e + k) : -1};
+        T ve[1] = {T(0)};
+        if (ce[0] >= 0) ve[0] = trsv_peek(S, ce[0]);
+        trsv_wait<1, T>(S, ce, ve, st, spin_ns);
+        if (ce[0] >= 0) acc += __ldg(M.val + e + k) * ve[0];
+      }
+#pragma unroll
+      for (int o = TRSV_LANES / 2; o > 0; o >>= 1) {
+        acc += __shfl_xor_sync(0xffffffffu, acc, o);
+#pragma unroll
+        for (int d = 0; d < TRSV_ROWS; d++) cf[d] += __shfl_xor_sync(0xffffffffu, cf[d], o);
+      }
+      // cf[d]: coefficient of the row d + 1 positions back; row q reaches the
+      // previous task's last row at distance q + 1 and row s of this task at
+      // distance q - s
+      T v = cur.rhs - acc;
+      T kp = T(0);
+#pragma unroll
+      for (int d = 0; d < TRSV_ROWS; d++)
+        if (d == q) kp = cf[d];
+      if (kp != T(0)) v -= kp * xprev;
+      if (cur.meta & 8) {
+#pragma unroll
+        for (int s = 0; s + 1 < TRSV_ROWS; s++) {
+          if (s + 1 >= cnt) break;
+          const T xs = __shfl_sync(0xffffffffu, v * cur.rdg, s * TRSV_LANES);
+          T ks = T(0);
+#pragma unroll
+          for (int d = 0; d < TRSV_ROWS; d++)
+            if (d == q - s - 1) ks = cf[d];
+          v -= ks * xs;
+        }
+      }
+      const T val = v * cur.rdg;
+      if (active && g == 0) {
+        stage[r - b0] = val;
+        st_relaxed(x + r, val);
+      }
+      xprev = __shfl_sync(0xffffffffu, val, (cnt - 1) * TRSV_LANES);
+    };
+    ChainPre<T> p0, p1;
+    int ti = t0;
+    chain_fetch<LOWER, T>(M, S, b0, base, wd, ti, q, g, rhs_of, p0);
+    for (;;) {
+      if (ti + 1 < t1) chain_fetch<LOWER, T>(M, S, b0, base, wd, ti + 1, q, g, rhs_of, p1);
+      process(p0);
+      if (ti + 1 >= t1) break;
+      if (ti + 2 < t1) chain_fetch<LOWER, T>(M, S, b0, base, wd, ti + 2, q, g, rhs_of, p0);
+      process(p1);
+      if (ti + 2 >= t1) break;
+      ti += 2;
     }
   }
   __syncthreads();

@@ -218,7 +218,17 @@ __device__ bool gram(const Dev<T> &D, Shared &sh, Ctl &ctl, int m, int k) {
 // backward results; no right-hand side is fetched from global memory on the
 // dependency chain.
 // ---------------------------------------------------------------------------
-extern __shared__ __align__(16) unsigned char nle_dyn_smem[];  // two slabs of the triangular solves
+extern __shared__ __align__(16) unsigned char nle_dyn_smem[];  // two slabs (and a halo) of the triangular solves
+
+// Schedule of the triangular solves compiled into this translation unit
+// (the build compiles every (precision, rows-per-thread) pair once per
+// schedule, so each kernel holds one solve only and keeps its registers);
+// the kernels carry it as a template argument so that the two builds'
+// kernels have distinct names.
+#ifndef NLE_CHAIN_TU
+#define NLE_CHAIN_TU 0
+#endif
+constexpr bool kChainTU = NLE_CHAIN_TU != 0;
 
 template <typename T>
 __device__ __forceinline__ void trsv_forward(const Dev<T> &D, Shared &sh, const Ctl &ctl, int k) {
@@ -234,8 +244,13 @@ __device__ __forceinline__ void trsv_forward(const Dev<T> &D, Shared &sh, const 
     for (int t = 0; t < k; t++) w -= T(sh.a[t]) * __ldcg(D.R + (int64_t)sh.order[t] * D.npad + b0 + i);
     bufB[i] = w;
   }
-  trsv_block<true, T>(L, D.z, D.npad, D.bsize, ctl.twarps, ctl.spin_ns, D.st, bufA,
-                      [&](int64_t r) { return bufB[r - b0]; });
+  if constexpr (kChainTU) {
+    const TriChain<T> C{D.Loff, D.Lw, D.Lcol, D.Lval, D.rdiag, D.Lwp, D.Ltask};
+    trsv_chain<true, T>(C, D.z, D.npad, D.bsize, ctl.spin_ns, D.st, bufA, [&](int64_t r) { return bufB[r - b0]; });
+  } else {
+    trsv_block<true, T>(L, D.z, D.npad, D.bsize, ctl.twarps, ctl.spin_ns, D.st, bufA, bufB + D.bsize, D.Lhoff,
+                        D.Lhcol, ctl.halo_k, ctl.halo_sleep_ns, [&](int64_t r) { return bufB[r - b0]; });
+  }
 }
 
 // The right-hand side of the backward solve is the forward result of the
@@ -247,8 +262,13 @@ __device__ __forceinline__ void trsv_backward(const Dev<T> &D, const Ctl &ctl) {
   const T *bufA = reinterpret_cast<const T *>(nle_dyn_smem);
   T *bufB = reinterpret_cast<T *>(nle_dyn_smem) + D.bsize;
   const int64_t b0 = (int64_t)grank() * D.bsize;
-  trsv_block<false, T>(U, D.c0, D.npad, D.bsize, ctl.twarps, ctl.spin_ns, D.st, bufB,
-                       [&](int64_t r) { return bufA[r - b0]; });
+  if constexpr (kChainTU) {
+    const TriChain<T> C{D.Uoff, D.Uw, D.Ucol, D.Uval, D.rdiag, D.Uwp, D.Utask};
+    trsv_chain<false, T>(C, D.c0, D.npad, D.bsize, ctl.spin_ns, D.st, bufB, [&](int64_t r) { return bufA[r - b0]; });
+  } else {
+    trsv_block<false, T>(U, D.c0, D.npad, D.bsize, ctl.twarps, ctl.spin_ns, D.st, bufB, bufB + D.bsize, D.Uhoff,
+                         D.Uhcol, ctl.halo_k, ctl.halo_sleep_ns, [&](int64_t r) { return bufA[r - b0]; });
+  }
 }
 
 template <typename T>
@@ -611,6 +631,8 @@ __device__ void load_state(const Dev<T> &D, Shared &sh, Ctl &ctl, const Opts &O,
   ctl.rbuf = 0;
   ctl.spin_ns = O.spin_ns;
   ctl.twarps = max(1, min(NWARP, O.trsv_warps));
+  ctl.halo_k = O.halo_k;
+  ctl.halo_sleep_ns = O.halo_sleep_ns;
   if (threadIdx.x == 0) {
     sh.ok = 1;
     for (int s = 0; s < KMAX; s++) sh.order[s] = s;
@@ -813,7 +835,7 @@ __device__ bool newton_body(const Dev<T> &D, const Opts &O, Shared &sh, Ctl &ctl
   return true;
 }
 
-template <typename T, int RPC>
+template <typename T, int RPC, int CH>
 __global__ void __launch_bounds__(TPB, 1) k_newton(Dev<T> D, Opts O) {
   __shared__ Shared sh;
   Ctl ctl;
@@ -1071,7 +1093,7 @@ __device__ bool dacg_body(const Dev<T> &D, const Opts &O, Shared &sh, Ctl &ctl, 
   return true;
 }
 
-template <typename T, int RPC>
+template <typename T, int RPC, int CH>
 __global__ void __launch_bounds__(TPB, 1) k_dacg(Dev<T> D, Opts O) {
   __shared__ Shared sh;
   Ctl ctl;
@@ -1084,7 +1106,7 @@ __global__ void __launch_bounds__(TPB, 1) k_dacg(Dev<T> D, Opts O) {
 // ---------------------------------------------------------------------------
 
 // y = (A - theta I) x  (x in D.p, y in D.y)
-template <typename T, int RPC>
+template <typename T, int RPC, int CH>
 __global__ void __launch_bounds__(TPB, 1) k_shifted(Dev<T> D, double theta) {
   constexpr int W = VT<T>::W;
   if (threadIdx.x == 0) {
@@ -1109,7 +1131,7 @@ __global__ void __launch_bounds__(TPB, 1) k_shifted(Dev<T> D, double theta) {
 
 // c = P_k g by Algorithm 3.1 (g in D.g, output in D.y); m columns of Q, k pairs
 // in slots 0..k-1 (chronological).
-template <typename T, int RPC>
+template <typename T, int RPC, int CH>
 __global__ void __launch_bounds__(TPB, 1) k_prec(Dev<T> D, Opts O, int m, int k) {
   constexpr int W = VT<T>::W;
   __shared__ Shared sh;
@@ -1149,7 +1171,7 @@ __global__ void __launch_bounds__(TPB, 1) k_prec(Dev<T> D, Opts O, int m, int k)
 }
 
 // One inner solve: theta given, r in rT, Q with m columns, k pairs in slots 0..k-1.
-template <typename T, int RPC>
+template <typename T, int RPC, int CH>
 __global__ void __launch_bounds__(TPB, 1) k_pcg(Dev<T> D, Opts O, int m, int k, double theta, int max_pcg) {
   __shared__ Shared sh;
   Ctl ctl;
@@ -1226,7 +1248,7 @@ __device__ void fp64_comb_add(const Dev<T> &D, int p, const double *coef, double
   }
 }
 
-template <typename T, int RPC>
+template <typename T, int RPC, int CH>
 __global__ void __launch_bounds__(TPB, 1) k_adjoint(Dev<T> D, Opts O, int j, int p, double tol, int max_refine) {
   constexpr int W = VT<T>::W;
   __shared__ Shared sh;
@@ -1423,7 +1445,7 @@ __device__ __forceinline__ bool group_sync(const Batch<T> &B, int group, unsigne
   return sh.ok != 0;
 }
 
-template <typename T, int RPC>
+template <typename T, int RPC, int CH>
 __global__ void __launch_bounds__(TPB, 1) k_batch(Batch<T> B, Opts O) {
   __shared__ Shared sh;
   __shared__ __align__(16) unsigned char sD_raw[sizeof(Dev<T>)];  // problem descriptor
@@ -1469,13 +1491,13 @@ __global__ void __launch_bounds__(TPB, 1) k_batch(Batch<T> B, Opts O) {
 #define NLE_CAT(a, b) NLE_CAT2(a, b)
 void *NLE_CAT(kernel_ptr_, NLE_TAG)(int id) {
   switch (id) {
-    case 0: return (void *)k_newton<NLE_T, NLE_RPC>;
-    case 1: return (void *)k_dacg<NLE_T, NLE_RPC>;
-    case 2: return (void *)k_shifted<NLE_T, NLE_RPC>;
-    case 3: return (void *)k_prec<NLE_T, NLE_RPC>;
-    case 4: return (void *)k_pcg<NLE_T, NLE_RPC>;
-    case 5: return (void *)k_adjoint<NLE_T, NLE_RPC>;
-    case 6: return (void *)k_batch<NLE_T, NLE_RPC>;
+    case 0: return (void *)k_newton<NLE_T, NLE_RPC, NLE_CHAIN_TU>;
+    case 1: return (void *)k_dacg<NLE_T, NLE_RPC, NLE_CHAIN_TU>;
+    case 2: return (void *)k_shifted<NLE_T, NLE_RPC, NLE_CHAIN_TU>;
+    case 3: return (void *)k_prec<NLE_T, NLE_RPC, NLE_CHAIN_TU>;
+    case 4: return (void *)k_pcg<NLE_T, NLE_RPC, NLE_CHAIN_TU>;
+    case 5: return (void *)k_adjoint<NLE_T, NLE_RPC, NLE_CHAIN_TU>;
+    case 6: return (void *)k_batch<NLE_T, NLE_RPC, NLE_CHAIN_TU>;
   }
   return nullptr;
 }

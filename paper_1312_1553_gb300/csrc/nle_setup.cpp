@@ -410,12 +410,225 @@ void build_sell(const Permuted &P, int H, int64_t bsize, bool level_rounds, Sell
 template void build_sell<float>(const Permuted &, int, int64_t, bool, SellSet<float> &);
 template void build_sell<double>(const Permuted &, int, int64_t, bool, SellSet<double> &);
 
+template <typename TV>
+int64_t build_halo(EllHost<TV> &E, int64_t npad, int64_t bsize, bool lower, int64_t hlimit, const std::vector<int32_t> &lev,
+                   int mind, std::vector<int64_t> &hoff, std::vector<int32_t> &hcol) {
+  const int64_t nl = (int64_t)lev.size();
+  const int64_t ns = (npad + bsize - 1) / bsize;
+  std::vector<int64_t> stamp(npad, -1), slot(npad, 0);
+  hoff.assign(ns + 1, 0);
+  hcol.clear();
+  int64_t hmax = 0;
+  for (int pass = 0; pass < 2; pass++) {
+    std::fill(stamp.begin(), stamp.end(), -1);
+    hcol.clear();
+    for (int64_t s = 0; s < ns; s++) {
+      const int64_t b0 = s * bsize, b1 = std::min(npad, b0 + bsize), w = E.width[s];
+      int64_t cnt = 0;
+      for (int64_t i = 0; i < b1 - b0; i++) {
+        const int64_t r = lower ? b0 + i : b1 - 1 - i;
+        const int64_t base = E.off[s] + (r - b0) * w;
+        for (int64_t k = 0; k < w; k++) {
+          const int64_t c = E.col[base + k];
+          if (c < 0 || (c >= b0 && c < b1)) continue;
+          if (r < nl && c < nl && lev[r] - lev[c] < mind) continue;
+          if (stamp[c] != s) {
+            stamp[c] = s;
+            slot[c] = cnt++;
+            if (pass == 1) hcol.push_back((int32_t)c);
+          }
+          if (pass == 1) E.col[base + k] = (int32_t)(TRSV_HALO + slot[c]);
+        }
+      }
+      hoff[s + 1] = hoff[s] + cnt;
+      hmax = std::max(hmax, cnt);
+    }
+    if (pass == 0 && hmax > hlimit) return -1;
+  }
+  return hmax;
+}
+
+template int64_t build_halo<float>(EllHost<float> &, int64_t, int64_t, bool, int64_t, const std::vector<int32_t> &,
+                                   int, std::vector<int64_t> &, std::vector<int32_t> &);
+template int64_t build_halo<double>(EllHost<double> &, int64_t, int64_t, bool, int64_t, const std::vector<int32_t> &,
+                                    int, std::vector<int64_t> &, std::vector<int32_t> &);
+
+template <typename TV>
+void build_chain(const Permuted &P, int64_t bsize, bool lower, int nwarps, ChainHost<TV> &out) {
+  const int64_t n = P.n, npad = P.npad;
+  const std::vector<int64_t> &rp = lower ? P.Lrp : P.Urp;
+  const std::vector<int32_t> &col = lower ? P.Lcol : P.Ucol;
+  const std::vector<double> &val = lower ? P.Lval : P.Uval;
+  const std::vector<int32_t> &lev = lower ? P.lev : P.levU;
+  const int64_t ns = (npad + bsize - 1) / bsize;
+  EllHost<TV> &E = out.ell;
+  E.off.assign(ns + 1, 0);
+  E.width.assign(ns, 8);
+  for (int64_t s = 0; s < ns; s++) {
+    int64_t w = 0;
+    for (int64_t r = s * bsize; r < std::min(n, (s + 1) * bsize); r++) w = std::max(w, rp[r + 1] - rp[r]);
+    w = std::max<int64_t>(8, (w + 7) / 8 * 8);
+    E.width[s] = (int32_t)w;
+    E.off[s + 1] = E.off[s] + (std::min(npad, (s + 1) * bsize) - s * bsize) * w;
+  }
+  E.col.assign(E.off[ns], -1);
+  E.val.assign(E.off[ns], TV(0));
+  E.round.clear();
+  out.wptr.assign(ns * (NWARP + 1), 0);
+  out.task.clear();
+  out.nstrands = 0;
+  // does row r depend on row q?  (columns ascending within a row)
+  auto dep = [&](int64_t r, int64_t q) {
+    if (r >= n || q < 0 || q >= n) return false;
+    return std::binary_search(col.begin() + rp[r], col.begin() + rp[r + 1], (int32_t)q);
+  };
+  std::vector<int64_t> tfirst;  // per task of the slab: processing index of its first row
+  std::vector<int> tcnt;
+  std::vector<int64_t> sfirst;  // per strand: first task
+  std::vector<int64_t> strand_of_row;
+  for (int64_t s = 0; s < ns; s++) {
+    const int64_t b0 = s * bsize, b1 = std::min(npad, b0 + bsize), nb = b1 - b0;
+    if (nb <= 0) continue;
+    auto row = [&](int64_t i) { return lower ? b0 + i : b1 - 1 - i; };
+    // tasks: a row that depends on its predecessor continues the current
+    // task; one that does not closes a task that holds such a link (a chain),
+    // while rows without links are packed TRSV_ROWS to a task
+    tfirst.clear();
+    tcnt.clear();
+    std::vector<char> tlinked;  // first row depends on the previous task's last row
+    for (int64_t i = 0; i < nb;) {
+      const bool linked = i > 0 && dep(row(i), row(i - 1));
+      bool chainlike = linked;
+      int cnt = 1;
+      tfirst.push_back(i);
+      tlinked.push_back(linked ? 1 : 0);
+      i++;
+      while (cnt < TRSV_ROWS && i < nb) {
+        const bool l = dep(row(i), row(i - 1));
+        if (!l && chainlike) break;
+        chainlike = chainlike || l;
+        cnt++;
+        i++;
+      }
+      tcnt.push_back(cnt);
+    }
+    const int64_t nt = (int64_t)tfirst.size();
+    // strands: runs of linked tasks
+    sfirst.clear();
+    for (int64_t t = 0; t < nt; t++)
+      if (!tlinked[t]) sfirst.push_back(t);
+    const int64_t nstr = (int64_t)sfirst.size();
+    sfirst.push_back(nt);
+    strand_of_row.assign(nb, 0);
+    for (int64_t k = 0; k < nstr; k++)
+      for (int64_t i = tfirst[sfirst[k]]; i < (sfirst[k + 1] < nt ? tfirst[sfirst[k + 1]] : nb); i++)
+        strand_of_row[i] = k;
+    // strand graph inside the slab and a topological order (Kahn) that takes
+    // the ready strand whose first row has the lowest level first
+    std::vector<std::vector<int64_t>> succ(nstr);
+    std::vector<int64_t> indeg(nstr, 0), deps;
+    for (int64_t k = 0; k < nstr; k++) {
+      deps.clear();
+      const int64_t i0 = tfirst[sfirst[k]], i1 = sfirst[k + 1] < nt ? tfirst[sfirst[k + 1]] : nb;
+      for (int64_t i = i0; i < i1; i++) {
+        const int64_t r = row(i);
+        if (r >= n) continue;
+        for (int64_t e = rp[r]; e < rp[r + 1]; e++) {
+          const int64_t c = col[e];
+          if (c < b0 || c >= b1) continue;
+          const int64_t ci = lower ? c - b0 : b1 - 1 - c;
+          const int64_t d = strand_of_row[ci];
+          if (d != k) deps.push_back(d);
+        }
+      }
+      std::sort(deps.begin(), deps.end());
+      deps.erase(std::unique(deps.begin(), deps.end()), deps.end());
+      for (int64_t d : deps) {
+        succ[d].push_back(k);
+        indeg[k]++;
+      }
+    }
+    auto key = [&](int64_t k) {
+      const int64_t r = row(tfirst[sfirst[k]]);
+      return std::make_pair(r < n ? (int64_t)lev[r] : (int64_t)0, tfirst[sfirst[k]]);
+    };
+    auto later = [&](int64_t a, int64_t b) { return key(a) > key(b); };
+    std::vector<int64_t> heap, order;
+    for (int64_t k = 0; k < nstr; k++)
+      if (!indeg[k]) heap.push_back(k);
+    std::make_heap(heap.begin(), heap.end(), later);
+    while (!heap.empty()) {
+      std::pop_heap(heap.begin(), heap.end(), later);
+      const int64_t k = heap.back();
+      heap.pop_back();
+      order.push_back(k);
+      for (int64_t j : succ[k])
+        if (--indeg[j] == 0) {
+          heap.push_back(j);
+          std::push_heap(heap.begin(), heap.end(), later);
+        }
+    }
+    // strands to warps, least loaded first (ties: lowest warp)
+    std::vector<std::vector<int64_t>> wl(nwarps);
+    std::vector<int64_t> load(nwarps, 0);
+    for (int64_t k : order) {
+      const int w = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+      wl[w].push_back(k);
+      load[w] += sfirst[k + 1] - sfirst[k];
+    }
+    // tasks warp by warp; entries of the current task and of the strand's
+    // previous task's last row become register-resolved markers
+    for (int w = 0; w < NWARP; w++) {
+      out.wptr[s * (NWARP + 1) + w] = (int32_t)(out.task.size() / 2);
+      if (w >= nwarps) continue;
+      for (int64_t k : wl[w])
+        for (int64_t t = sfirst[k]; t < sfirst[k + 1]; t++) {
+          const int64_t i0 = tfirst[t];
+          const int cnt = tcnt[t];
+          const int64_t prevlast = (t > sfirst[k]) ? row(i0 - 1) : -1;
+          bool seq = false;
+          for (int a = 0; a < cnt; a++) {
+            const int64_t r = row(i0 + a);
+            if (r >= n) continue;
+            const int64_t base = E.off[s] + (r - b0) * E.width[s];
+            int64_t slot = 0;
+            // markers first (they must sit in the first entries of the row)
+            for (int pass = 0; pass < 2; pass++)
+              for (int64_t e = rp[r]; e < rp[r + 1]; e++) {
+                const int64_t c = col[e];
+                int d = 0;
+                for (int a2 = 0; a2 < a; a2++)
+                  if (row(i0 + a2) == c) d = a - a2;
+                if (d == 0 && c == prevlast) d = a + 1;
+                if ((pass == 0) != (d > 0)) continue;
+                E.col[base + slot] = d > 0 ? -2 - d : (int32_t)c;
+                E.val[base + slot] = TV(val[e]);
+                slot++;
+                if (d > 0 && d <= a) seq = true;
+              }
+          }
+          out.task.push_back((int32_t)row(i0));
+          out.task.push_back(cnt | (seq ? 8 : 0));
+        }
+    }
+    out.wptr[s * (NWARP + 1) + NWARP] = (int32_t)(out.task.size() / 2);
+    out.nstrands += nstr;
+  }
+}
+
+template void build_chain<float>(const Permuted &, int64_t, bool, int, ChainHost<float> &);
+template void build_chain<double>(const Permuted &, int64_t, bool, int, ChainHost<double> &);
+
 void permute(int64_t n, const int64_t *rp, const int32_t *ci, const double *va, const Factor &F,
              const std::vector<int32_t> &perm, const std::vector<int32_t> &iperm, int64_t npad, Permuted &P) {
   P.n = n;
   P.npad = npad;
   P.lev.assign(n, 0);
-  for (int64_t i = 0; i < n; i++) P.lev[i] = F.levL[perm[i]];
+  P.levU.assign(n, 0);
+  for (int64_t i = 0; i < n; i++) {
+    P.lev[i] = F.levL[perm[i]];
+    P.levU[i] = F.levU[perm[i]];
+  }
   // A' = P A P^T, rows sorted by new column
   std::vector<std::pair<int32_t, double>> tmp;
   P.Arp.assign(n + 1, 0);

@@ -26,7 +26,8 @@ struct Permuted {
   std::vector<int64_t> Arp, Lrp, Urp;
   std::vector<int32_t> Acol, Lcol, Ucol;
   std::vector<double> Aval, Lval, Uval, diag;
-  std::vector<int32_t> lev;  // level (of L) of every relabelled row
+  std::vector<int32_t> lev;   // level (of L) of every relabelled row
+  std::vector<int32_t> levU;  // level (of U = L^T) of every relabelled row
 };
 
 template <typename TV>
@@ -45,6 +46,22 @@ struct EllHost {
   std::vector<int32_t> col;    // -1 = padding
   std::vector<TV> val;
   std::vector<uint8_t> round;  // per row: its round inside its group of TRSV_ROWS rows
+};
+
+// Chain schedule of one strictly triangular factor (see trsv_chain): the
+// rows of each slab are cut into tasks of at most TRSV_ROWS consecutive rows
+// (in processing order: ascending for L, descending for U); consecutive tasks
+// whose first row depends on the previous task's last row form a strand,
+// which one warp solves task after task with that dependency held in
+// registers.  Strands are dealt to the warps of the slab's CTA in a
+// topological order of the strand graph, so every wait ends.
+template <typename TV>
+struct ChainHost {
+  EllHost<TV> ell;            // per-slab ELL; an entry resolved in registers carries col = -2 - d,
+                              // d = distance back in the warp's processing order (1..TRSV_ROWS)
+  std::vector<int32_t> wptr;  // per slab: NWARP + 1 offsets into task (warp w: [wptr[w], wptr[w+1]))
+  std::vector<int32_t> task;  // per task: first row processed, rows | (sequential ? 8 : 0)
+  int64_t nstrands = 0;
 };
 
 template <typename TV>
@@ -83,5 +100,25 @@ void permute(int64_t n, const int64_t *rp, const int32_t *ci, const double *va, 
 // when dependencies can point to later slabs; see trsv_block).
 template <typename TV>
 void build_sell(const Permuted &P, int H, int64_t bsize, bool level_rounds, SellSet<TV> &S);
+
+// Halo of the level schedule: per slab, the distinct entries of E that point
+// outside the slab (device positions), in the order the slab's processing
+// (ascending rows for L, descending for U) first needs them; hoff: ns + 1
+// offsets into hcol.  When the longest list is at most hlimit, E's columns
+// of those entries become TRSV_HALO + slot and the longest length is
+// returned; otherwise E is left unchanged and -1 is returned.
+// Only entries whose row lies at least mind levels above their column
+// (lev: levels of the factor's solve order, per device position) go
+// through the halo; the others stay global reads.
+template <typename TV>
+int64_t build_halo(EllHost<TV> &E, int64_t npad, int64_t bsize, bool lower, int64_t hlimit, const std::vector<int32_t> &lev,
+                   int mind, std::vector<int64_t> &hoff, std::vector<int32_t> &hcol);
+
+// Chain schedule of the strictly lower (lower = true: P.Lrp/Lcol/Lval, levels
+// P.lev) or upper (P.Urp/Ucol/Uval, levels P.levU) factor for nwarps warps
+// per slab.  Needs the identity relabelling (slabs are ranges of the
+// factored matrix's own row order).
+template <typename TV>
+void build_chain(const Permuted &P, int64_t bsize, bool lower, int nwarps, ChainHost<TV> &out);
 
 }  // namespace nle

@@ -25,6 +25,8 @@ STATUS = {0: "NLE_OK", 1: "NLE_ERR_ARG", 2: "NLE_ERR_CSR", 3: "NLE_ERR_NOT_SPD",
 NLE_FP64, NLE_MIXED = 0, 1
 NLE_ORDER_NATURAL, NLE_ORDER_MULTICOLOR1, NLE_ORDER_MULTICOLOR2 = 0, 1, 2
 NLE_BFGS_SIMPLIFIED, NLE_BFGS_FULL = 0, 1
+NLE_SCHED_AUTO, NLE_SCHED_LEVEL, NLE_SCHED_CHAIN = 0, 1, 2
+SCHEDULES = {1: "level", 2: "chain"}
 EXITS = ("tol", "maxit", "eigres", "stagnation", "breakdown")
 PHASES = ("spmv", "update", "fwd_solve", "bwd_solve", "dots", "direction", "outer_fp64", "other")
 NLE_MAX_P = 64
@@ -41,7 +43,8 @@ class nle_options(ctypes.Structure):
                 ("max_dacg", ctypes.c_int), ("precision", ctypes.c_int), ("exit_eigres", ctypes.c_int),
                 ("exit_stagnation", ctypes.c_int), ("dacg_recompute", ctypes.c_int),
                 ("spin_timeout_s", ctypes.c_double), ("grid_ctas", ctypes.c_int), ("trsv_warps", ctypes.c_int),
-                ("ordering", ctypes.c_int), ("bfgs_update", ctypes.c_int)]
+                ("ordering", ctypes.c_int), ("bfgs_update", ctypes.c_int), ("trsv_schedule", ctypes.c_int),
+                ("trsv_halo", ctypes.c_int), ("halo_window", ctypes.c_int), ("halo_backoff_ns", ctypes.c_int)]
 
 
 class nle_stats(ctypes.Structure):
@@ -53,7 +56,8 @@ class nle_stats(ctypes.Structure):
                 ("pcg_iterations", ctypes.c_int64), ("pcg_sum_m", ctypes.c_int64), ("pcg_sum_k", ctypes.c_int64),
                 ("dacg_iterations", ctypes.c_int64), ("dacg_sum_m", ctypes.c_int64),
                 ("kernel_launches", ctypes.c_int64), ("ms_phase", ctypes.c_double * 8), ("ascending", ctypes.c_int),
-                ("ms_batch", ctypes.c_double)]
+                ("ms_batch", ctypes.c_double), ("trsv_schedule", ctypes.c_int), ("tune_ms_level", ctypes.c_double),
+                ("tune_ms_chain", ctypes.c_double), ("strands", ctypes.c_int64)]
 
 
 class nle_pcg_info(ctypes.Structure):
@@ -366,7 +370,8 @@ def stats_dict(s: nle_stats) -> dict:
                 pcg_sum_k=int(s.pcg_sum_k), dacg_iterations=int(s.dacg_iterations), dacg_sum_m=int(s.dacg_sum_m),
                 kernel_launches=int(s.kernel_launches),
                 ms_phase=dict(zip(PHASES, [float(x) for x in s.ms_phase])), ascending=bool(s.ascending),
-                ms_batch=float(s.ms_batch))
+                ms_batch=float(s.ms_batch), trsv_schedule=SCHEDULES.get(int(s.trsv_schedule), "none"),
+                tune_ms=dict(level=float(s.tune_ms_level), chain=float(s.tune_ms_chain)), strands=int(s.strands))
 
 
 def _eigsh_function():

@@ -1,0 +1,47 @@
+// Host-only test shim: runs the library's own host set-up code (the IC
+// factor and the chain schedule of its triangular solves, nle_setup.cpp)
+// without a GPU, so tests/test_chain_schedule.py can check the schedule on
+// the CPU.  Built by that test with g++; not part of the library.
+#include <cstring>
+#include <vector>
+
+#include "../paper_1312_1553_gb300/csrc/nle_internal.h"
+#include "../paper_1312_1553_gb300/csrc/nle_setup.h"
+
+using namespace nle;
+
+static Factor g_F;
+static Permuted g_P;
+static ChainHost<double> g_C[2];
+
+extern "C" int shim_factor(int64_t n, const int64_t *rp, const int32_t *ci, const double *va, int lfil, double tau) {
+  int64_t bad = -1;
+  if (ic_factor_host(n, rp, ci, va, lfil, tau, g_F, &bad) != 0) return -1;
+  std::vector<int32_t> perm(n), iperm(n);
+  for (int64_t i = 0; i < n; i++) perm[i] = iperm[i] = (int32_t)i;
+  const int64_t npad = (n + 127) / 128 * 128;
+  permute(n, rp, ci, va, g_F, perm, iperm, npad, g_P);
+  return 0;
+}
+
+// Build the chain schedule of L (lower = 1) or U (0); returns the number of
+// tasks and the ELL size through *nent.
+extern "C" int64_t shim_chain(int lower, int64_t bsize, int nwarps, int64_t *nent, int64_t *nslab) {
+  ChainHost<double> &C = g_C[lower ? 1 : 0];
+  build_chain<double>(g_P, bsize, lower != 0, nwarps, C);
+  *nent = (int64_t)C.ell.col.size();
+  *nslab = (int64_t)C.ell.width.size();
+  return (int64_t)C.task.size() / 2;
+}
+
+extern "C" void shim_chain_get(int lower, int64_t *off, int32_t *width, int32_t *col, double *val, int32_t *wptr,
+                               int32_t *task, double *diag) {
+  ChainHost<double> &C = g_C[lower ? 1 : 0];
+  memcpy(off, C.ell.off.data(), C.ell.off.size() * 8);
+  memcpy(width, C.ell.width.data(), C.ell.width.size() * 4);
+  memcpy(col, C.ell.col.data(), C.ell.col.size() * 4);
+  memcpy(val, C.ell.val.data(), C.ell.val.size() * 8);
+  memcpy(wptr, C.wptr.data(), C.wptr.size() * 4);
+  memcpy(task, C.task.data(), C.task.size() * 4);
+  memcpy(diag, g_P.diag.data(), g_P.diag.size() * 8);
+}

@@ -3,7 +3,12 @@
 Every value comes from the oracle (``oracle/``) run on the seeded workloads
 of ``workloads/``; nothing here calls the CUDA library.  Usage:
 
-    python tests/golden/make_golden.py diff3d7_100 [more workload names]
+    python tests/golden/make_golden.py [--threads T] [--out DIR] diff3d7_100 [more workload names]
+
+--threads fixes the BLAS thread count of the oracle's dot products (the
+summation order, hence the last bits, depends on it; on the 27-point
+workload's eigenvalue cluster 18-20 that changes the Newton path); the count
+used is stored in the file.
 
 Each run writes tests/golden/<name>.json with the eigenvalues, the oracle's
 iteration counts, a seeded sample of eigenvector entries and a seeded
@@ -72,7 +77,11 @@ def hex_kappa_gradient(A, lam, V):
 SKETCH_K = 256
 
 
-def main(names):
+def main(names, threads=None, out_dir=HERE):
+    if threads:
+        from threadpoolctl import threadpool_limits
+
+        threadpool_limits(limits=threads, user_api="blas")
     for name in names:
         A, st = W.workload(name)
         p = st["p"]
@@ -89,7 +98,8 @@ def main(names):
                    sample_V=[[float(V[i, j]) for i in idx] for j in range(p)],
                    oracle_seconds=sec, oracle_stats={k: stats[k] for k in
                                                      ("dacg_its", "outer_its", "pcg_its", "converged", "final_res",
-                                                      "ascending", "nnz_L", "sigma")})
+                                                      "ascending", "nnz_L", "sigma")},
+                   blas_threads=threads)
         # CountSketch of every eigenvector (sign convention applied): the
         # full-size tests compare sketches, which estimate ||v_gpu - v_oracle||
         bucket, sign = W.count_sketch_hash(A.n, SKETCH_K, st["seed"])
@@ -99,10 +109,17 @@ def main(names):
             out.update(kappa_gradient(A, lam, V, opt))
         if name.startswith("hex27"):
             out.update(hex_kappa_gradient(A, lam, V))
-        with open(os.path.join(HERE, f"{name}.json"), "w") as fh:
+        with open(os.path.join(out_dir, f"{name}.json"), "w") as fh:
             json.dump(out, fh, indent=1)
         print(name, sec, lam)
 
 
 if __name__ == "__main__":
-    main(sys.argv[1:])
+    import argparse
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--threads", type=int, default=None)
+    ap.add_argument("--out", default=HERE)
+    ap.add_argument("names", nargs="+")
+    a = ap.parse_args()
+    main(a.names, a.threads, a.out)

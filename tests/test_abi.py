@@ -43,6 +43,7 @@ def test_default_options(lib):
     o = nle.nle_default_options()
     assert o.k_max == 5 and o.tau_pcg == 1e-2 and o.tau_dacg == 1e-2 and o.max_dacg == 5000
     assert o.precision == nle.NLE_FP64 and o.exit_eigres == 1 and o.exit_stagnation == 1
+    assert o.trsv_schedule == nle.NLE_SCHED_AUTO and o.trsv_warps == 16
 
 
 def _create(A, opt=None):
@@ -66,6 +67,10 @@ def test_argument_errors_without_device(lib):
     o.k_max = 99
     st, h, msg = _create(A, o)
     assert st == 1 and "k_max" in msg
+    o = nle.nle_default_options()
+    o.trsv_schedule = 7
+    st, h, msg = _create(A, o)
+    assert st == 1 and "trsv_schedule" in msg
 
 
 @pytest.mark.parametrize("case", ["unsorted", "asym", "nodiag", "negdiag"])

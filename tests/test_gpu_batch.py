@@ -23,7 +23,8 @@ def test_batch_matches_single_and_oracle(nle, prec):
     sizes = [2400, 5200, 3100, 7000, 2000, 4300]
     mats = [W.geometric_graph_laplacian(n, 900 + i) for i, n in enumerate(sizes)]
     p = 4
-    opts = dict(precision=nle.NLE_MIXED if prec == "mixed" else nle.NLE_FP64, grid_ctas=4)
+    opts = dict(precision=nle.NLE_MIXED if prec == "mixed" else nle.NLE_FP64, grid_ctas=4,
+                trsv_schedule=nle.NLE_SCHED_LEVEL)
     solvers = []
     X0s = []
     for i, A in enumerate(mats):
@@ -79,7 +80,7 @@ def test_batch_groups_of_eight_fp64(nle):
     p = 3
     solvers, X0s = [], []
     for i, A in enumerate(mats):
-        s = nle.Eigensolver(A, dict(precision=nle.NLE_FP64, grid_ctas=8))
+        s = nle.Eigensolver(A, dict(precision=nle.NLE_FP64, grid_ctas=8, trsv_schedule=nle.NLE_SCHED_LEVEL))
         s.factor_ic(30, 1e-2)
         solvers.append(s)
         X0s.append(W.start_vectors(A.n, p, 720 + i))
@@ -113,7 +114,8 @@ def test_batch_on_non_blocking_stream(nle):
     with torch.cuda.stream(stream):
         solvers, X0s = [], []
         for i, A in enumerate(mats):
-            s = nle.Eigensolver(A, dict(precision=nle.NLE_FP64, grid_ctas=4), stream=stream)
+            s = nle.Eigensolver(A, dict(precision=nle.NLE_FP64, grid_ctas=4, trsv_schedule=nle.NLE_SCHED_LEVEL),
+                                stream=stream)
             s.factor_ic(30, 1e-2)
             solvers.append(s)
             X0s.append(W.start_vectors(A.n, p, 740 + i))
@@ -138,7 +140,8 @@ def test_batch_bounded_wait_reports_timeout_and_context_survives(nle):
     X0s = [W.start_vectors(A.n, p, 760 + i) for i, A in enumerate(mats)]
     bad = []
     for A in mats:
-        s = nle.Eigensolver(A, dict(precision=nle.NLE_MIXED, grid_ctas=4, spin_timeout_s=1e-9))
+        s = nle.Eigensolver(A, dict(precision=nle.NLE_MIXED, grid_ctas=4, spin_timeout_s=1e-9,
+                                    trsv_schedule=nle.NLE_SCHED_LEVEL))
         s.factor_ic(30, 1e-2)
         bad.append(s)
     with pytest.raises(nle.NLEError) as e:
@@ -148,7 +151,7 @@ def test_batch_bounded_wait_reports_timeout_and_context_survives(nle):
         s.close()
     good = []
     for A in mats:
-        s = nle.Eigensolver(A, dict(precision=nle.NLE_MIXED, grid_ctas=4))
+        s = nle.Eigensolver(A, dict(precision=nle.NLE_MIXED, grid_ctas=4, trsv_schedule=nle.NLE_SCHED_LEVEL))
         s.factor_ic(30, 1e-2)
         good.append(s)
     lams, Vs, per = nle.batch_solve(good, p, 1e-8, 100, 20, X0s)

@@ -17,6 +17,7 @@ import os
 import numpy as np
 import pytest
 
+import fullsize_checks as FC
 import oracle as O
 import workloads as W
 
@@ -134,7 +135,7 @@ def _pairs_and_Q(A, k, m, seed):
 
 
 @pytest.mark.parametrize("prec", PRECS)
-@pytest.mark.parametrize("k,m", [(0, 0), (0, 3), (1, 1), (3, 2), (5, 4)])
+@pytest.mark.parametrize("k,m", [(0, 0), (0, 3), (1, 1), (3, 2), (5, 4), (9, 2), (10, 5)])
 def test_apply_prec(nle, prec, k, m):
     A, st = load("diff3d7_24")
     s = solver(nle, A, prec)
@@ -316,9 +317,39 @@ def test_full_bfgs_update_matches_oracle(nle, name, prec):
 
 
 @pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("kmax,update", [(10, "simplified"), (9, "full")])
+def test_solve_largest_pair_rings(nle, kmax, update, prec):
+    """The largest ring of stored pairs (k_max = NLE_MAX_KMAX) and, with the
+    full BFGS update, the largest ring plus its staging slot (k_max =
+    NLE_MAX_KMAX - 1), against the oracle run with the same k_max and
+    update.  Two inner iterations per Newton step make every eigenpair take
+    more than k_max outer steps, so the ring wraps around."""
+    A, st = load("diff3d7_24")
+    p = st["p"]
+    X0 = W.start_vectors(A.n, p, st["seed"])
+    full = update == "full"
+    s = solver(nle, A, prec, k_max=kmax, bfgs_update=nle.NLE_BFGS_FULL if full else nle.NLE_BFGS_SIMPLIFIED)
+    s.factor_ic(st["lfil"], st["tau_ic"])
+    lam, V, stats = s.solve(p, st["tol"], 100, 2, X0)
+    lam = lam.cpu().numpy()
+    V = V.cpu().numpy()
+    s.close()
+    opt = O.OracleOptions(tol=st["tol"], lfil=st["lfil"], tau_ic=st["tau_ic"], k_max=kmax, bfgs_full=full,
+                          max_pcg=2)
+    lref, Vref, rstats = O.dacg_newton(A, p, X0, opt)
+    np.testing.assert_allclose(lam, lref, rtol=1e-10 if prec == "fp64" else 1e-8)
+    for j in range(p):
+        assert sin_angle(V[j], Vref[:, j]) <= 1e-6
+    _check_solution(A, lam, V, st["tol"])
+    assert max(rstats["outer_its"]) > kmax and max(stats["outer_its"]) > kmax
+
+
+@pytest.mark.parametrize("prec", PRECS)
 def test_solve_full_size_100cubed(nle, prec):
     """n = 1e6, p = 10, IC(10, 1e-3), tol 1e-8: eigenvalues against the stored
-    oracle run, eigenvector samples, residuals and orthogonality at full size."""
+    oracle run, eigenvector samples, whole eigenvectors through their sketches
+    (within the residual bound, and within 1e-6 wherever that bound is below
+    1e-6), residuals and orthogonality at full size."""
     with open(os.path.join(HERE, "golden", "diff3d7_100.json")) as fh:
         gold = json.load(fh)
     A, st = load("diff3d7_100")
@@ -335,6 +366,10 @@ def test_solve_full_size_100cubed(nle, prec):
         ref = np.array(gold["sample_V"][j])
         v = align(V[j, idx], ref)
         assert np.abs(v - ref).max() <= 2e-6
+    ang, bnd = FC.check_eigenvectors(A, V, gold, stats["final_res"], f"diff3d7_100 {prec}")
+    # the stated eigenvector tolerance, 1e-6, wherever the residual bound
+    # allows it
+    assert np.all(ang[bnd <= 1e-6] <= 1e-6), ang
     _check_solution(A, lam, V, st["tol"])
     s.close()
 
@@ -343,10 +378,13 @@ def test_solve_full_size_hex27_96(nle):
     """n = 884,736 (27-point trilinear hex stiffness), p = 20, IC(20, 1e-4),
     mixed precision: eigenvalues against the stored oracle run; eigenvector
     samples within 10 tol lambda_j / gap_j (the eigenvector error allowed by
-    the residual test ||A v - lambda v|| <= tol lambda, on either side);
-    residuals, orthogonality, order; and the eigenvalue backward against the
+    the residual test ||A v - lambda v|| <= tol lambda, on either side) and
+    whole eigenvectors through their sketches within the residual bound;
+    residuals, orthogonality, order; the eigenvalue backward against the
     identity sum_e A_e d(sum lambda)/dA_e = sum lambda (Rayleigh quotients
-    are homogeneous of degree 1 in the entries)."""
+    are homogeneous of degree 1 in the entries); and the backward carried to
+    the element coefficients (the paper-scale case of a loss on element
+    parameters) against the oracle's."""
     import torch
 
     with open(os.path.join(HERE, "golden", "hex27_96.json")) as fh:
@@ -370,8 +408,27 @@ def test_solve_full_size_hex27_96(nle):
         ref = np.array(gold["sample_V"][j])
         v = align(V[j, idx], ref)
         assert np.abs(v - ref).max() <= 10 * st["tol"] * glam[j] / gaps[j], j
+    ang, bnd = FC.check_eigenvectors(A, V, gold, stats["final_res"], "hex27_96 mixed")
+    assert np.all(ang[bnd <= 1e-6] <= 1e-6), ang
     _check_solution(A, lam, V, st["tol"])
     assert abs(float(A.val @ grad) - lam.sum()) <= 1e-9 * lam.sum()
+    # the backward of sum lambda_j with respect to the element coefficients
+    # (chain rule through the hex assembly): the oracle's at 64 elements, its
+    # norm, and the Euler identity sum_e kappa_e dL/dkappa_e = sum lambda_j
+    kt = torch.tensor(A.meta["kappa"], dtype=torch.float64, requires_grad=True)
+    (gk,) = torch.autograd.grad(W.hex_poisson_values_torch(kt), kt, grad_outputs=torch.tensor(grad))
+    gk = gk.numpy().ravel()
+    elems = np.array(gold["grad_elems"])
+    ref = np.array(gold["grad_kappa"])
+    # each term v_j v_j^T is off by at most twice its eigenvector's angle
+    # (bounded above); the sum over the pairs by their sum
+    gtol = 2 * float(np.sum(bnd))
+    gerr = np.linalg.norm(gk[elems] - ref) / np.linalg.norm(ref)
+    print(f"element gradient: relative error {gerr:.2e} (bound {gtol:.2e}), "
+          f"norm {np.linalg.norm(gk):.6e} vs {gold['grad_kappa_norm']:.6e}")
+    assert gerr <= gtol, (gerr, gtol)
+    assert abs(np.linalg.norm(gk) - gold["grad_kappa_norm"]) <= gtol * gold["grad_kappa_norm"]
+    assert abs(float(A.meta["kappa"].ravel() @ gk) - lam.sum()) <= 1e-9 * lam.sum()
 
 
 # ---------------------------------------------------------------------------
