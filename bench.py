@@ -66,9 +66,6 @@ def parse():
                     help="outer step cap; 0 = the workload's (the paper's ITMAX = 100; 400 for workloads with "
                          "eigenvalue clusters)")
     ap.add_argument("--spin-timeout", type=float, default=0.0, help="0 = library default (seconds)")
-    ap.add_argument("--halo", type=int, default=-1, help="level schedule: -1 library default; 0 solving warps read "
-                                                         "off-slab values themselves; d >= 1 a copy warp stages those "
-                                                         "at least d levels back")
     ap.add_argument("--schedule", default="auto", choices=["auto", "level", "chain"],
                     help="schedule of the triangular solves (auto = timed at set-up, the faster kept)")
     ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
@@ -507,8 +504,6 @@ def main():
     opts["bfgs_update"] = nle.NLE_BFGS_FULL if args.bfgs == "full" else nle.NLE_BFGS_SIMPLIFIED
     opts["trsv_schedule"] = {"auto": nle.NLE_SCHED_AUTO, "level": nle.NLE_SCHED_LEVEL,
                              "chain": nle.NLE_SCHED_CHAIN}[args.schedule]
-    if args.halo >= 0:
-        opts["trsv_halo"] = args.halo
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         s = nle.Eigensolver(A, opts, stream=stream)
@@ -651,7 +646,7 @@ def main():
                             n=A.n, nnz=A.nnz, p=p, lfil=st["lfil"], tau_ic=st["tau_ic"], tol=st["tol"],
                             precision="FP32 bulk + FP64 outer step" if prec == nle.NLE_MIXED else "FP64",
                             nnz_L=nnz_l, nlev_L=F["nlevL"], ordering=args.ordering, bfgs=args.bfgs, ic_seconds=ic_seconds,
-                            trsv_schedule=all_stats[-1]["trsv_schedule"], schedule_request=args.schedule, halo=args.halo,
+                            trsv_schedule=all_stats[-1]["trsv_schedule"], schedule_request=args.schedule,
                             tune_ms=all_stats[-1]["tune_ms"], strands=all_stats[-1]["strands"],
                             l2="working set > 129 MB L2 (no flush needed)",
                             parallelism=f"replicas{world}" if world > 1 else "single GPU"),

@@ -102,21 +102,14 @@ typedef struct {
                             nle_multicolor_order; applied before the IC factor */
   int bfgs_update;       /* NLE_BFGS_SIMPLIFIED (default) or NLE_BFGS_FULL */
   int trsv_schedule;     /* NLE_SCHED_AUTO (default), NLE_SCHED_LEVEL or NLE_SCHED_CHAIN */
-  int trsv_halo;         /* level schedule, natural ordering: 0 (default) every solving warp
-                            reads the values its slab needs from other slabs in global
-                            memory itself; d >= 1: those that lie at least d levels below
-                            the row needing them are copied into shared memory by the
-                            CTA's last warp as they are published (when the lists fit in
-                            192 KB with the slab buffers) */
-  int halo_window;       /* halo copy warp: values in flight per lane, 1..8 (default 4) */
-  int halo_backoff_ns;   /* halo copy warp: pause after a sweep that moved nothing (default 0) */
 } nle_options;
 
 /* Schedule of the triangular solves of Phat_0 = (L L^T)^{-1} (Section 2).
  * Both give the same solution (up to rounding order); they differ in how
  * the rows are dealt to the GPU's warps:
  *   NLE_SCHED_LEVEL  rows of each CTA's slab sorted by level of L, groups
- *                    of 4 same-level rows per warp step;
+ *                    of 4 rows per warp step, every row polling its own
+ *                    inputs (no barrier between levels);
  *   NLE_SCHED_CHAIN  the factored matrix's own row order; runs of rows in
  *                    which each row depends on its predecessor (the grid
  *                    lines of a stencil matrix in natural order) stay on one

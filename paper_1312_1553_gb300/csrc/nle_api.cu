@@ -190,8 +190,6 @@ struct nle_ctx {
   DBuf A_sptr, A_col, A_val, A64_val, d_diag;
   DBuf L_off, L_w, L_col, L_val, L_round, U_off, U_w, U_col, U_val, U_round;
   DBuf L_wp, L_task, U_wp, U_task;  // chain schedule: per-warp task lists
-  DBuf L_hoff, L_hcol, U_hoff, U_hcol;  // level schedule: per-slab halo lists
-  int64_t hmax = 0;                      // longest halo list (0: no halo)
   int chain = 0;                     // schedule of the triangular solves in use (1 = chain)
   double tune_ms[2] = {0.0, 0.0};    // measured application time of the level / chain schedule
   int64_t nstrands = 0;
@@ -290,13 +288,6 @@ static Dev<T> make_dev(nle_t h) {
   D.Uwp = h->U_wp.as<int32_t>();
   D.Ltask = h->L_task.as<int2>();
   D.Utask = h->U_task.as<int2>();
-  D.hmax = h->hmax;
-  if (h->hmax > 0) {
-    D.Lhoff = h->L_hoff.as<int64_t>();
-    D.Uhoff = h->U_hoff.as<int64_t>();
-    D.Lhcol = h->L_hcol.as<int32_t>();
-    D.Uhcol = h->U_hcol.as<int32_t>();
-  }
   const int64_t np = h->npad, ext = h->npad + 32 * h->vw;
   T *v = h->vecs.as<T>();
   D.p = v + 0 * np;
@@ -339,8 +330,6 @@ static Opts make_opts(nle_t h, double tol, int max_newton, int max_pcg) {
   O.recompute = h->opt.dacg_recompute;
   O.spin_ns = (long long)(h->opt.spin_timeout_s * 1e9);
   O.trsv_warps = h->opt.trsv_warps;
-  O.halo_k = std::max(1, std::min(8, h->opt.halo_window));
-  O.halo_sleep_ns = std::max(0, h->opt.halo_backoff_ns);
   O.bfgs_full = h->opt.bfgs_update == NLE_BFGS_FULL ? 1 : 0;
   return O;
 }
@@ -351,8 +340,7 @@ static nle_status launch(nle_t h, int id, void **args) {
   void *fn = kernel_ptr<T>(id, h->rpc, h->chain);
   if (!fn) return fail(h, NLE_ERR_ARG, "no kernel instance for this size");
   // dynamic shared memory: two slab-sized buffers of the triangular solves
-  // and the halo buffer
-  const size_t dyn = (2 * (size_t)h->bsize + (size_t)h->hmax) * (mixed(h) ? 4 : 8);
+  const size_t dyn = 2 * (size_t)h->bsize * (mixed(h) ? 4 : 8);
   NLE_CUDA(h, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
   int nb = 0;
   NLE_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, TPB, dyn));
@@ -444,27 +432,6 @@ static nle_status upload_layout(nle_t h, const Permuted &P, bool level_rounds, i
     NLE_CUDA(h, upload(h->U_task, CU.task, h->stream));
     S.L.round.assign(1, 0);
     S.U.round.assign(1, 0);
-  }
-  h->hmax = 0;
-  if (!chain && !level_rounds && h->opt.trsv_halo) {
-    // halo lists when they fit in shared memory beside the two slab buffers
-    const int64_t limit = (int64_t)(192 * 1024 / sizeof(TV)) - 2 * h->bsize;
-    std::vector<int64_t> lo, uo;
-    std::vector<int32_t> lc, uc;
-    const int64_t hl = build_halo<TV>(S.L, h->npad, h->bsize, true, limit, P.lev, h->opt.trsv_halo, lo, lc);
-    if (hl >= 0) {
-      const int64_t hu = build_halo<TV>(S.U, h->npad, h->bsize, false, limit, P.levU, h->opt.trsv_halo, uo, uc);
-      if (hu < 0) {
-        // undo L's remapping: rebuild its ELL
-        build_sell<TV>(P, H, h->bsize, level_rounds, S);
-      } else {
-        h->hmax = std::max<int64_t>(1, std::max(hl, hu));
-        NLE_CUDA(h, upload(h->L_hoff, lo, h->stream));
-        NLE_CUDA(h, upload(h->L_hcol, lc, h->stream));
-        NLE_CUDA(h, upload(h->U_hoff, uo, h->stream));
-        NLE_CUDA(h, upload(h->U_hcol, uc, h->stream));
-      }
-    }
   }
   NLE_CUDA(h, upload(h->L_off, S.L.off, h->stream));
   NLE_CUDA(h, upload(h->L_w, S.L.width, h->stream));
@@ -564,9 +531,6 @@ void nle_default_options(nle_options *o) {
   o->ordering = NLE_ORDER_NATURAL;
   o->bfgs_update = NLE_BFGS_SIMPLIFIED;
   o->trsv_schedule = NLE_SCHED_AUTO;
-  o->trsv_halo = 0;
-  o->halo_window = 4;
-  o->halo_backoff_ns = 0;
 }
 
 const char *nle_last_error(nle_t h) { return h ? h->err.c_str() : g_create_error.c_str(); }
@@ -1109,7 +1073,7 @@ static nle_status batch_impl(int count, nle_t *hs, int p, double tol, int max_ne
     NLE_CUDA(h0, cudaMemsetAsync(h->state.p, 0, sizeof(State), h->stream));
     NLE_CUDA(h0, cudaStreamSynchronize(h->stream));
     while ((int64_t)rpc * h->grid * TPB < h->nchunks) rpc *= 2;
-    dyn = std::max(dyn, (2 * (size_t)h->bsize + (size_t)h->hmax) * sizeof(T));
+    dyn = std::max(dyn, 2 * (size_t)h->bsize * sizeof(T));
     order[b] = b;
   }
   if (rpc > 8) return fail(h0, NLE_ERR_ARG, "a problem is too large for its CTA group");

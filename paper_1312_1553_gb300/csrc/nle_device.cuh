@@ -167,7 +167,6 @@ struct Ctl {
   int rbuf;        // reduction buffer parity
   long long spin_ns;
   int twarps;      // warps of this CTA that take part in the triangular solves
-  int halo_k, halo_sleep_ns;
 };
 
 // Phase timers: CTA 0 / thread 0 charges the time since the last mark to
@@ -391,14 +390,11 @@ __device__ __forceinline__ void trsv_fetch(const TriEll<T> &M, int64_t b0, int64
 
 // Where a triangular solve reads its dependencies: its CTA's slab [b0, b1)
 // of the output x is copied in shared memory (stage); a dependency in
-// another slab is either read from global memory or, when the factor's
-// entries were remapped to a halo (column = TRSV_HALO + slot), from the
-// CTA's shared-memory halo buffer, which its copy warp fills.
+// another slab is read from global memory.
 template <typename T>
 struct TriSrc {
   const T *x;
   const volatile T *stage;
-  const volatile T *halo;
   int64_t b0, b1;
 };
 
@@ -407,7 +403,6 @@ struct TriSrc {
 template <typename T>
 __device__ __forceinline__ T trsv_peek(const TriSrc<T> &S, int c) {
   if (c >= S.b0 && c < S.b1) return S.stage[c - S.b0];
-  if (c >= TRSV_HALO) return S.halo[c - TRSV_HALO];
   return ld_relaxed(S.x + c);
 }
 
@@ -446,101 +441,18 @@ __device__ __forceinline__ void trsv_wait(const TriSrc<T> &S, const int *c, T *v
   }
 }
 
-// Copy warp of the halo: lane l moves halo entries l, l + 32, ... (in the
-// order the slab first needs them) from global memory into shared memory as
-// their producers publish them, HALO_K loads in flight per lane, so that
-// the solving warps never wait on a global-memory round trip for a value
-// that is already there.  Its waits end because every halo value comes from
-// a slab that does not depend on this one (lower slabs for L, higher for
-// L^T); they are also bounded in time (reset by every completed entry),
-// after which the remaining entries are set to 0 and NLE_ERR_TIMEOUT is
-// recorded.
-constexpr int HALO_K = 8;
-
-template <typename T>
-__device__ __forceinline__ void halo_copy(const T *x, volatile T *halo, const int32_t *hcol, int hcnt, State *st,
-                                          long long spin_ns, int K, int sleep_ns) {
-  const int lane = threadIdx.x & 31;
-  int idx[HALO_K];
-  T v[HALO_K];
-  int nxt = lane;
-#pragma unroll
-  for (int k = 0; k < HALO_K; k++) {
-    idx[k] = -1;
-    v[k] = T(0);
-    if (k < K && nxt < hcnt) {
-      idx[k] = nxt;
-      v[k] = ld_relaxed(x + __ldg(hcol + nxt));
-      nxt += 32;
-    }
-  }
-  long long t0 = 0;
-  int spins = 0;
-  for (;;) {
-    bool any = false, moved = false;
-#pragma unroll
-    for (int k = 0; k < HALO_K; k++) {
-      if (idx[k] < 0) continue;
-      if (!is_sent(v[k])) {
-        halo[idx[k]] = v[k];
-        moved = true;
-        idx[k] = -1;
-        if (nxt < hcnt) {
-          idx[k] = nxt;
-          v[k] = ld_relaxed(x + __ldg(hcol + nxt));
-          nxt += 32;
-        }
-      } else {
-        v[k] = ld_relaxed(x + __ldg(hcol + idx[k]));
-      }
-      any = any || idx[k] >= 0;
-    }
-    if (!any) break;
-    if (!moved && sleep_ns > 0) __nanosleep(sleep_ns);
-    if (moved) {
-      t0 = 0;
-      spins = 0;
-    } else if (++spins >= 64) {
-      spins = 0;
-      const long long now = gtimer();
-      if (t0 == 0) {
-        t0 = now;
-      } else if (now - t0 > spin_ns) {
-        record_error(st, 8 /*NLE_ERR_TIMEOUT*/, 103);
-#pragma unroll
-        for (int k = 0; k < HALO_K; k++)
-          if (idx[k] >= 0) halo[idx[k]] = T(0);
-        for (; nxt < hcnt; nxt += 32) halo[nxt] = T(0);
-        break;
-      }
-    }
-  }
-}
-
 template <bool LOWER, typename T, typename RHS>
 __device__ __forceinline__ void trsv_block(const TriEll<T> &M, T *x, int64_t npad, int64_t bsize, int twarps,
-                                           long long spin_ns, State *st, T *stage_mem, T *halo_mem,
-                                           const int64_t *hoff, const int32_t *hcol, int halo_k, int halo_sleep_ns,
-                                           RHS rhs_of) {
+                                           long long spin_ns, State *st, T *stage_mem, RHS rhs_of) {
   const int64_t b0 = (int64_t)grank() * bsize;
   const int64_t b1 = min(npad, b0 + bsize);
   const int64_t nb = b1 > b0 ? b1 - b0 : 0;
   volatile T *stage = stage_mem;
-  volatile T *halo = halo_mem;
   const T sent = sentinel<T>();
   for (int64_t i = threadIdx.x; i < nb; i += blockDim.x) stage[i] = sent;
-  // halo mode: the last warp copies the slab's halo, the others solve
-  int64_t h0 = 0, hcnt = 0;
-  if (hcol && nb > 0) {
-    h0 = __ldg(hoff + grank());
-    hcnt = __ldg(hoff + grank() + 1) - h0;
-    twarps = min(twarps, NWARP - 1);
-    for (int64_t i = threadIdx.x; i < hcnt; i += blockDim.x) halo[i] = sent;
-  }
   __syncthreads();
-  const TriSrc<T> S{x, stage, halo, b0, b1};
+  const TriSrc<T> S{x, stage, b0, b1};
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (hcnt > 0 && warp == NWARP - 1) halo_copy<T>(x, halo, hcol + h0, (int)hcnt, st, spin_ns, halo_k, halo_sleep_ns);
   const int64_t ngrp = nb / TRSV_ROWS;
   int64_t it = warp;
   if (warp < twarps && it < ngrp) {
@@ -690,7 +602,7 @@ __device__ __forceinline__ void trsv_chain(const TriChain<T> &M, T *x, int64_t n
   const T sent = sentinel<T>();
   for (int64_t i = threadIdx.x; i < nb; i += blockDim.x) stage[i] = sent;
   __syncthreads();
-  const TriSrc<T> S{x, stage, nullptr, b0, b1};
+  const TriSrc<T> S{x, stage, b0, b1};
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // a CTA past the last slab has no rows (and no task offsets)
   const int t0 = nb > 0 ? __ldg(M.wptr + grank() * (NWARP + 1) + warp) : 0;

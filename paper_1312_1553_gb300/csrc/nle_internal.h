@@ -39,8 +39,6 @@ constexpr int TRSV_ROWS = NLE_TRSV_ROWS;
 constexpr int TRSV_LANES = 32 / TRSV_ROWS;
 constexpr int TRSV_EPL = 16 / TRSV_LANES;
 static_assert(TRSV_ROWS == 4 || TRSV_ROWS == 8, "4 or 8 rows per warp");
-// column offset of halo slots in the level schedule's factor entries (n < 2^30)
-constexpr int TRSV_HALO = 1 << 30;
 
 template <typename T>
 struct Sell {
@@ -102,8 +100,6 @@ struct Opts {
   int recompute;
   long long spin_ns;
   int trsv_warps;     // warps per CTA that take part in the triangular solves
-  int halo_k;         // halo copy warp: entries in flight per lane (1..8)
-  int halo_sleep_ns;  // halo copy warp: pause after a sweep that moved nothing
   int bfgs_full;      // 1: pairs (s_k, r_k - r_{k+1}) (full BFGS update), 0: (s_k, r_k)
 };
 
@@ -133,14 +129,6 @@ struct Dev {
   int chain = 0;
   const int32_t *Lwp = nullptr, *Uwp = nullptr;
   const int2 *Ltask = nullptr, *Utask = nullptr;
-  // level schedule with a halo (Lhcol != nullptr): the entries of L (U) that
-  // point outside the row's slab carry column TRSV_HALO + slot, slot into
-  // the slab's halo list Lhcol[Lhoff[s] .. Lhoff[s+1]) of device positions
-  // (in the order the slab first needs them), copied into shared memory by
-  // the CTA's last warp; hmax = the longest halo list
-  const int64_t *Lhoff = nullptr, *Uhoff = nullptr;
-  const int32_t *Lhcol = nullptr, *Uhcol = nullptr;
-  int64_t hmax = 0;
   // working-precision vectors (npad; z and c0 have npad + 32*VW entries)
   T *p, *y, *s, *g, *z, *c0, *rT, *x, *Ax, *Ap;
   const T *X0 = nullptr;  // optional: start vectors (p columns, device order) for the whole-solve kernel

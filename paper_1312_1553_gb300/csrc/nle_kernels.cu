@@ -218,7 +218,7 @@ __device__ bool gram(const Dev<T> &D, Shared &sh, Ctl &ctl, int m, int k) {
 // backward results; no right-hand side is fetched from global memory on the
 // dependency chain.
 // ---------------------------------------------------------------------------
-extern __shared__ __align__(16) unsigned char nle_dyn_smem[];  // two slabs (and a halo) of the triangular solves
+extern __shared__ __align__(16) unsigned char nle_dyn_smem[];  // two slabs of the triangular solves
 
 // Schedule of the triangular solves compiled into this translation unit
 // (the build compiles every (precision, rows-per-thread) pair once per
@@ -248,8 +248,8 @@ __device__ __forceinline__ void trsv_forward(const Dev<T> &D, Shared &sh, const 
     const TriChain<T> C{D.Loff, D.Lw, D.Lcol, D.Lval, D.rdiag, D.Lwp, D.Ltask};
     trsv_chain<true, T>(C, D.z, D.npad, D.bsize, ctl.spin_ns, D.st, bufA, [&](int64_t r) { return bufB[r - b0]; });
   } else {
-    trsv_block<true, T>(L, D.z, D.npad, D.bsize, ctl.twarps, ctl.spin_ns, D.st, bufA, bufB + D.bsize, D.Lhoff,
-                        D.Lhcol, ctl.halo_k, ctl.halo_sleep_ns, [&](int64_t r) { return bufB[r - b0]; });
+    trsv_block<true, T>(L, D.z, D.npad, D.bsize, ctl.twarps, ctl.spin_ns, D.st, bufA,
+                        [&](int64_t r) { return bufB[r - b0]; });
   }
 }
 
@@ -266,8 +266,8 @@ __device__ __forceinline__ void trsv_backward(const Dev<T> &D, const Ctl &ctl) {
     const TriChain<T> C{D.Uoff, D.Uw, D.Ucol, D.Uval, D.rdiag, D.Uwp, D.Utask};
     trsv_chain<false, T>(C, D.c0, D.npad, D.bsize, ctl.spin_ns, D.st, bufB, [&](int64_t r) { return bufA[r - b0]; });
   } else {
-    trsv_block<false, T>(U, D.c0, D.npad, D.bsize, ctl.twarps, ctl.spin_ns, D.st, bufB, bufB + D.bsize, D.Uhoff,
-                         D.Uhcol, ctl.halo_k, ctl.halo_sleep_ns, [&](int64_t r) { return bufA[r - b0]; });
+    trsv_block<false, T>(U, D.c0, D.npad, D.bsize, ctl.twarps, ctl.spin_ns, D.st, bufB,
+                         [&](int64_t r) { return bufA[r - b0]; });
   }
 }
 
@@ -631,8 +631,6 @@ __device__ void load_state(const Dev<T> &D, Shared &sh, Ctl &ctl, const Opts &O,
   ctl.rbuf = 0;
   ctl.spin_ns = O.spin_ns;
   ctl.twarps = max(1, min(NWARP, O.trsv_warps));
-  ctl.halo_k = O.halo_k;
-  ctl.halo_sleep_ns = O.halo_sleep_ns;
   if (threadIdx.x == 0) {
     sh.ok = 1;
     for (int s = 0; s < KMAX; s++) sh.order[s] = s;

@@ -411,49 +411,6 @@ template void build_sell<float>(const Permuted &, int, int64_t, bool, SellSet<fl
 template void build_sell<double>(const Permuted &, int, int64_t, bool, SellSet<double> &);
 
 template <typename TV>
-int64_t build_halo(EllHost<TV> &E, int64_t npad, int64_t bsize, bool lower, int64_t hlimit, const std::vector<int32_t> &lev,
-                   int mind, std::vector<int64_t> &hoff, std::vector<int32_t> &hcol) {
-  const int64_t nl = (int64_t)lev.size();
-  const int64_t ns = (npad + bsize - 1) / bsize;
-  std::vector<int64_t> stamp(npad, -1), slot(npad, 0);
-  hoff.assign(ns + 1, 0);
-  hcol.clear();
-  int64_t hmax = 0;
-  for (int pass = 0; pass < 2; pass++) {
-    std::fill(stamp.begin(), stamp.end(), -1);
-    hcol.clear();
-    for (int64_t s = 0; s < ns; s++) {
-      const int64_t b0 = s * bsize, b1 = std::min(npad, b0 + bsize), w = E.width[s];
-      int64_t cnt = 0;
-      for (int64_t i = 0; i < b1 - b0; i++) {
-        const int64_t r = lower ? b0 + i : b1 - 1 - i;
-        const int64_t base = E.off[s] + (r - b0) * w;
-        for (int64_t k = 0; k < w; k++) {
-          const int64_t c = E.col[base + k];
-          if (c < 0 || (c >= b0 && c < b1)) continue;
-          if (r < nl && c < nl && lev[r] - lev[c] < mind) continue;
-          if (stamp[c] != s) {
-            stamp[c] = s;
-            slot[c] = cnt++;
-            if (pass == 1) hcol.push_back((int32_t)c);
-          }
-          if (pass == 1) E.col[base + k] = (int32_t)(TRSV_HALO + slot[c]);
-        }
-      }
-      hoff[s + 1] = hoff[s] + cnt;
-      hmax = std::max(hmax, cnt);
-    }
-    if (pass == 0 && hmax > hlimit) return -1;
-  }
-  return hmax;
-}
-
-template int64_t build_halo<float>(EllHost<float> &, int64_t, int64_t, bool, int64_t, const std::vector<int32_t> &,
-                                   int, std::vector<int64_t> &, std::vector<int32_t> &);
-template int64_t build_halo<double>(EllHost<double> &, int64_t, int64_t, bool, int64_t, const std::vector<int32_t> &,
-                                    int, std::vector<int64_t> &, std::vector<int32_t> &);
-
-template <typename TV>
 void build_chain(const Permuted &P, int64_t bsize, bool lower, int nwarps, ChainHost<TV> &out) {
   const int64_t n = P.n, npad = P.npad;
   const std::vector<int64_t> &rp = lower ? P.Lrp : P.Urp;

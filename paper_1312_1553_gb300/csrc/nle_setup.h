@@ -101,19 +101,6 @@ void permute(int64_t n, const int64_t *rp, const int32_t *ci, const double *va, 
 template <typename TV>
 void build_sell(const Permuted &P, int H, int64_t bsize, bool level_rounds, SellSet<TV> &S);
 
-// Halo of the level schedule: per slab, the distinct entries of E that point
-// outside the slab (device positions), in the order the slab's processing
-// (ascending rows for L, descending for U) first needs them; hoff: ns + 1
-// offsets into hcol.  When the longest list is at most hlimit, E's columns
-// of those entries become TRSV_HALO + slot and the longest length is
-// returned; otherwise E is left unchanged and -1 is returned.
-// Only entries whose row lies at least mind levels above their column
-// (lev: levels of the factor's solve order, per device position) go
-// through the halo; the others stay global reads.
-template <typename TV>
-int64_t build_halo(EllHost<TV> &E, int64_t npad, int64_t bsize, bool lower, int64_t hlimit, const std::vector<int32_t> &lev,
-                   int mind, std::vector<int64_t> &hoff, std::vector<int32_t> &hcol);
-
 // Chain schedule of the strictly lower (lower = true: P.Lrp/Lcol/Lval, levels
 // P.lev) or upper (P.Urp/Ucol/Uval, levels P.levU) factor for nwarps warps
 // per slab.  Needs the identity relabelling (slabs are ranges of the

@@ -43,8 +43,7 @@ class nle_options(ctypes.Structure):
                 ("max_dacg", ctypes.c_int), ("precision", ctypes.c_int), ("exit_eigres", ctypes.c_int),
                 ("exit_stagnation", ctypes.c_int), ("dacg_recompute", ctypes.c_int),
                 ("spin_timeout_s", ctypes.c_double), ("grid_ctas", ctypes.c_int), ("trsv_warps", ctypes.c_int),
-                ("ordering", ctypes.c_int), ("bfgs_update", ctypes.c_int), ("trsv_schedule", ctypes.c_int),
-                ("trsv_halo", ctypes.c_int), ("halo_window", ctypes.c_int), ("halo_backoff_ns", ctypes.c_int)]
+                ("ordering", ctypes.c_int), ("bfgs_update", ctypes.c_int), ("trsv_schedule", ctypes.c_int)]
 
 
 class nle_stats(ctypes.Structure):
