@@ -102,6 +102,11 @@ typedef struct {
                             nle_multicolor_order; applied before the IC factor */
   int bfgs_update;       /* NLE_BFGS_SIMPLIFIED (default) or NLE_BFGS_FULL */
   int trsv_schedule;     /* NLE_SCHED_AUTO (default), NLE_SCHED_LEVEL or NLE_SCHED_CHAIN */
+  int trsv_poll_ns;      /* pause (ns, 0..10000) a warp of the triangular solves takes between
+                            two polls of inputs that are not ready (default 0: none) */
+  int trsv_rows;         /* level schedule: rows a warp takes at a time, 4 (8 lanes per row)
+                            or 2 (16 lanes, for factors with wide rows); 0 (default): chosen
+                            by the autotuner under NLE_SCHED_AUTO, 4 otherwise */
 } nle_options;
 
 /* Schedule of the triangular solves of Phat_0 = (L L^T)^{-1} (Section 2).
@@ -116,8 +121,10 @@ typedef struct {
  *                    warp, which resolves that dependency in registers;
  *                    needs the natural ordering;
  *   NLE_SCHED_AUTO   nle_factor_ic times one application of (L L^T)^{-1}
- *                    with each schedule on the device and keeps the faster
- *                    (the level schedule under a multicolour ordering).
+ *                    on the device with the level schedule at 4 and at 2
+ *                    rows per warp step (nle_options.trsv_rows) and with
+ *                    the chain schedule (natural ordering only), and keeps
+ *                    the fastest.
  * The choice and the timings are reported in nle_stats. */
 #define NLE_SCHED_AUTO 0
 #define NLE_SCHED_LEVEL 1
@@ -170,8 +177,10 @@ typedef struct {
                                    problem (nle_batch_solve; 0 after nle_solve) */
   int trsv_schedule;            /* NLE_SCHED_LEVEL or NLE_SCHED_CHAIN: the schedule in use */
   double tune_ms_level;         /* autotuner: device ms of one (L L^T)^{-1} application with */
-  double tune_ms_chain;         /*   each schedule (0 when not timed) */
+  double tune_ms_chain;         /*   each candidate (0 when not timed): level schedule with 4 */
+  double tune_ms_level2;        /*   rows per warp step, chain schedule, level with 2 rows */
   int64_t strands;              /* chain schedule: strands of L (runs of dependent rows) */
+  int trsv_rows;                /* level schedule: rows per warp step in use */
 } nle_stats;
 
 /* Parameters and outcome of one inner solve (nle_pcg). */

@@ -191,7 +191,8 @@ struct nle_ctx {
   DBuf L_off, L_w, L_col, L_val, L_round, U_off, U_w, U_col, U_val, U_round;
   DBuf L_wp, L_task, U_wp, U_task;  // chain schedule: per-warp task lists
   int chain = 0;                     // schedule of the triangular solves in use (1 = chain)
-  double tune_ms[2] = {0.0, 0.0};    // measured application time of the level / chain schedule
+  int trows = TRSV_ROWS;             // level schedule: rows a warp takes at a time (4 or 2)
+  double tune_ms[3] = {0.0, 0.0, 0.0};  // measured application time: level (4 rows), chain, level (2 rows)
   int64_t nstrands = 0;
   DBuf vecs;   // working-precision vectors
   DBuf vec64;  // Au, r, t
@@ -284,6 +285,7 @@ static Dev<T> make_dev(nle_t h) {
   D.Uround = h->U_round.as<uint8_t>();
   D.rdiag = h->d_diag.as<T>();
   D.chain = h->chain;
+  D.trows = h->trows;
   D.Lwp = h->L_wp.as<int32_t>();
   D.Uwp = h->U_wp.as<int32_t>();
   D.Ltask = h->L_task.as<int2>();
@@ -330,6 +332,7 @@ static Opts make_opts(nle_t h, double tol, int max_newton, int max_pcg) {
   O.recompute = h->opt.dacg_recompute;
   O.spin_ns = (long long)(h->opt.spin_timeout_s * 1e9);
   O.trsv_warps = h->opt.trsv_warps;
+  O.poll_ns = std::max(0, std::min(10000, h->opt.trsv_poll_ns));
   O.bfgs_full = h->opt.bfgs_update == NLE_BFGS_FULL ? 1 : 0;
   return O;
 }
@@ -412,7 +415,7 @@ template <typename TV>
 static nle_status upload_layout(nle_t h, const Permuted &P, bool level_rounds, int chain) {
   const int H = 32 * h->vw;
   SellSet<TV> S;
-  build_sell<TV>(P, H, h->bsize, level_rounds, S);
+  build_sell<TV>(P, H, h->bsize, level_rounds, h->trows, S);
   NLE_CUDA(h, upload(h->A_sptr, S.A.sptr, h->stream));
   NLE_CUDA(h, upload(h->A_col, S.A.col, h->stream));
   NLE_CUDA(h, upload(h->A_val, S.A.val, h->stream));
@@ -449,7 +452,8 @@ static nle_status upload_layout(nle_t h, const Permuted &P, bool level_rounds, i
 }
 
 static nle_status build_layout(nle_t h, const std::vector<int32_t> &P0, const int64_t *rp, const int32_t *ci,
-                               const double *va, int chain) {
+                               const double *va, int chain, int trows = TRSV_ROWS) {
+  h->trows = chain ? TRSV_ROWS : trows;
   if (chain) {
     h->perm.resize(h->n);
     h->iperm.resize(h->n);
@@ -487,6 +491,9 @@ static nle_status time_precond_t(nle_t h, double *ms) {
   k_gather<T><<<1024, 256, 0, h->stream>>>(D.g, h->scratch.as<double>(), h->d_perm.as<int32_t>(), h->n, h->npad);
   NLE_CUDA(h, cudaGetLastError());
   Opts O = make_opts(h, 1e-8, 1, 1);
+  // the timing runs are the library's own: their waits are bounded by at
+  // least 2 s whatever the caller's limit for its solves
+  O.spin_ns = std::max(O.spin_ns, 2000000000LL);
   NLE_CUDA(h, cudaMemsetAsync(h->state.p, 0, sizeof(State), h->stream));
   int m = 0, k = 0;
   void *args[] = {&D, &O, &m, &k};
@@ -531,6 +538,8 @@ void nle_default_options(nle_options *o) {
   o->ordering = NLE_ORDER_NATURAL;
   o->bfgs_update = NLE_BFGS_SIMPLIFIED;
   o->trsv_schedule = NLE_SCHED_AUTO;
+  o->trsv_poll_ns = 0;
+  o->trsv_rows = 0;
 }
 
 const char *nle_last_error(nle_t h) { return h ? h->err.c_str() : g_create_error.c_str(); }
@@ -563,6 +572,8 @@ nle_status nle_create(int64_t n, int64_t nnz, const int64_t *rowptr, const int32
     return fail(nullptr, NLE_ERR_ARG, "unknown ordering");
   if (h->opt.trsv_schedule < NLE_SCHED_AUTO || h->opt.trsv_schedule > NLE_SCHED_CHAIN)
     return fail(nullptr, NLE_ERR_ARG, "unknown trsv_schedule");
+  if (h->opt.trsv_rows != 0 && h->opt.trsv_rows != 2 && h->opt.trsv_rows != 4)
+    return fail(nullptr, NLE_ERR_ARG, "trsv_rows must be 0 (tuned), 2 or 4");
   if (h->opt.bfgs_update != NLE_BFGS_SIMPLIFIED && h->opt.bfgs_update != NLE_BFGS_FULL)
     return fail(nullptr, NLE_ERR_ARG, "unknown bfgs_update");
   if (h->opt.bfgs_update == NLE_BFGS_FULL && h->opt.k_max > NLE_MAX_KMAX - 1)
@@ -689,23 +700,39 @@ nle_status nle_factor_ic(nle_t h, int lfil, double tau_ic) {
   nle_status s = ensure_q(h, 8);
   if (s != NLE_OK) return s;
   // schedule of the triangular solves: the chain schedule needs the factored
-  // matrix's own row order (natural ordering); NLE_SCHED_AUTO times one
-  // preconditioner application with each schedule and keeps the faster
+  // matrix's own row order (natural ordering); the level schedule takes 4
+  // rows per warp step (8 lanes and 16 entries of a row in flight) or 2 (16
+  // lanes, 32 entries: factors with wide rows).  NLE_SCHED_AUTO times one
+  // preconditioner application with each candidate (level with 4 rows,
+  // chain, level with 2 rows) and keeps the fastest; an explicit
+  // trsv_rows fixes the rows of the level schedule.
   const bool chain_ok = P0.empty();
   int sched = h->opt.trsv_schedule;
   if (sched == NLE_SCHED_CHAIN && !chain_ok)
     return fail(h, NLE_ERR_ARG, "the chain schedule needs the natural ordering");
-  h->tune_ms[0] = h->tune_ms[1] = 0.0;
-  if (sched == NLE_SCHED_AUTO && chain_ok) {
-    for (int c = 0; c < 2; c++) {
-      if ((s = build_layout(h, P0, rp, ci, va, c)) != NLE_OK) return s;
-      if ((s = time_precond(h, &h->tune_ms[c])) != NLE_OK) return s;
+  h->tune_ms[0] = h->tune_ms[1] = h->tune_ms[2] = 0.0;
+  const int rows_opt = h->opt.trsv_rows;
+  if (sched == NLE_SCHED_AUTO) {
+    struct Cand {
+      int chain, rows, slot;
+    };
+    std::vector<Cand> cands;
+    if (rows_opt == 0 || rows_opt == 4) cands.push_back({0, 4, 0});
+    if (chain_ok) cands.push_back({1, TRSV_ROWS, 1});
+    if (rows_opt == 0 || rows_opt == 2) cands.push_back({0, 2, 2});
+    int best = -1;
+    for (size_t c = 0; c < cands.size(); c++) {
+      if ((s = build_layout(h, P0, rp, ci, va, cands[c].chain, cands[c].rows)) != NLE_OK) return s;
+      if ((s = time_precond(h, &h->tune_ms[cands[c].slot])) != NLE_OK) return s;
+      if (best < 0 || h->tune_ms[cands[c].slot] < h->tune_ms[cands[best].slot]) best = (int)c;
     }
-    // the chain layout is in place; go back to the level layout if it was faster
-    sched = h->tune_ms[1] < h->tune_ms[0] ? NLE_SCHED_CHAIN : NLE_SCHED_LEVEL;
-    if (sched == NLE_SCHED_LEVEL && (s = build_layout(h, P0, rp, ci, va, 0)) != NLE_OK) return s;
+    // the last candidate's layout is in place; rebuild the fastest one
+    if (best != (int)cands.size() - 1 &&
+        (s = build_layout(h, P0, rp, ci, va, cands[best].chain, cands[best].rows)) != NLE_OK)
+      return s;
   } else {
-    if ((s = build_layout(h, P0, rp, ci, va, sched == NLE_SCHED_CHAIN ? 1 : 0)) != NLE_OK) return s;
+    if ((s = build_layout(h, P0, rp, ci, va, sched == NLE_SCHED_CHAIN ? 1 : 0, rows_opt == 2 ? 2 : 4)) != NLE_OK)
+      return s;
   }
   NLE_CUDA(h, cudaStreamSynchronize(h->stream));
   h->factored = true;
@@ -766,8 +793,10 @@ static void fill_stats(const State &st, int p, double ms_dacg, double ms_newton,
 // schedule of the handle's triangular solves and the autotuner's timings
 static void schedule_stats(nle_t h, nle_stats *stats) {
   stats->trsv_schedule = h->chain ? NLE_SCHED_CHAIN : NLE_SCHED_LEVEL;
+  stats->trsv_rows = h->trows;
   stats->tune_ms_level = h->tune_ms[0];
   stats->tune_ms_chain = h->tune_ms[1];
+  stats->tune_ms_level2 = h->tune_ms[2];
   stats->strands = h->chain ? h->nstrands : 0;
 }
 

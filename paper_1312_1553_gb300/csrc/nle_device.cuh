@@ -167,6 +167,7 @@ struct Ctl {
   int rbuf;        // reduction buffer parity
   long long spin_ns;
   int twarps;      // warps of this CTA that take part in the triangular solves
+  int poll_ns;     // pause between two polls of a triangular-solve wait
 };
 
 // Phase timers: CTA 0 / thread 0 charges the time since the last mark to
@@ -353,7 +354,8 @@ struct TriEll {
   const int32_t *col;    // -1 = padding
   const T *val;
   const T *rdiag;         // npad: reciprocal pivots 1 / L_rr
-  const uint8_t *round;   // npad: round of the row inside its group of TRSV_ROWS rows
+  const uint8_t *round;   // npad: round of the row inside its group of rows
+  int rows;               // rows a warp takes at a time: 4 (8 lanes per row) or 2 (16 lanes)
 };
 
 template <typename T>
@@ -366,17 +368,17 @@ struct TriPre {
 
 template <bool LOWER, typename T, typename RHS>
 __device__ __forceinline__ void trsv_fetch(const TriEll<T> &M, int64_t b0, int64_t base, int wd, int64_t ngrp,
-                                           int64_t it, int q, int g, RHS &rhs_of, TriPre<T> &P) {
+                                           int64_t it, int q, int g, int lanes, RHS &rhs_of, TriPre<T> &P) {
   const int64_t gi = LOWER ? it : ngrp - 1 - it;
-  const int64_t r = b0 + TRSV_ROWS * gi + q;
+  const int64_t r = b0 + (int64_t)M.rows * gi + q;
   const int64_t e = base + (r - b0) * wd + g;
 #pragma unroll
   for (int k = 0; k < TRSV_EPL; k++) {
     P.c[k] = -1;
     P.a[k] = T(0);
-    if (g + k * TRSV_LANES < wd) {
-      P.c[k] = __ldg(M.col + e + k * TRSV_LANES);
-      P.a[k] = __ldg(M.val + e + k * TRSV_LANES);
+    if (g + k * lanes < wd) {
+      P.c[k] = __ldg(M.col + e + k * lanes);
+      P.a[k] = __ldg(M.val + e + k * lanes);
     }
   }
   P.rnd = __ldg(M.round + r);
@@ -411,7 +413,8 @@ __device__ __forceinline__ T trsv_peek(const TriSrc<T> &S, int c) {
 // only after 2^20 rounds of polling; past spin_ns the wait records
 // NLE_ERR_TIMEOUT and substitutes 0 so that dependants still finish.
 template <int N, typename T>
-__device__ __forceinline__ void trsv_wait(const TriSrc<T> &S, const int *c, T *v, State *st, long long spin_ns) {
+__device__ __forceinline__ void trsv_wait(const TriSrc<T> &S, const int *c, T *v, State *st, long long spin_ns,
+                                          int poll_ns = 0) {
   auto ready = [&]() {
     bool ok = true;
 #pragma unroll
@@ -427,6 +430,7 @@ __device__ __forceinline__ void trsv_wait(const TriSrc<T> &S, const int *c, T *v
       if (c[k] >= 0 && is_sent(v[k])) v[k] = trsv_peek(S, c[k]);
     ok = ready();
     if (__all_sync(0xffffffffu, ok)) return;
+    if (poll_ns > 0) __nanosleep(poll_ns);
     if (it >= (1 << 20)) {
       if (it == (1 << 20)) t0 = clock64();
       const bool late = clock64() - t0 > spin_ns * 21 / 10;  // cycles at about 2.1 GHz
@@ -443,7 +447,7 @@ __device__ __forceinline__ void trsv_wait(const TriSrc<T> &S, const int *c, T *v
 
 template <bool LOWER, typename T, typename RHS>
 __device__ __forceinline__ void trsv_block(const TriEll<T> &M, T *x, int64_t npad, int64_t bsize, int twarps,
-                                           long long spin_ns, State *st, T *stage_mem, RHS rhs_of) {
+                                           long long spin_ns, int poll_ns, State *st, T *stage_mem, RHS rhs_of) {
   const int64_t b0 = (int64_t)grank() * bsize;
   const int64_t b1 = min(npad, b0 + bsize);
   const int64_t nb = b1 > b0 ? b1 - b0 : 0;
@@ -453,17 +457,19 @@ __device__ __forceinline__ void trsv_block(const TriEll<T> &M, T *x, int64_t npa
   __syncthreads();
   const TriSrc<T> S{x, stage, b0, b1};
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t ngrp = nb / TRSV_ROWS;
+  const int R = M.rows;                    // 4 or 2; bsize is a multiple of 4
+  const int lanes = 32 / R;                // lanes per row
+  const int64_t ngrp = nb / R;
   int64_t it = warp;
   if (warp < twarps && it < ngrp) {
-    const int q = lane / TRSV_LANES, g = lane % TRSV_LANES;
+    const int q = lane / lanes, g = lane % lanes;
     const int64_t base = __ldg(M.off + grank());
     const int wd = __ldg(M.width + grank());
     // one group: its rounds, each a warp-uniform wait, the reduction and the
     // publication of the round's rows
     auto process = [&](const TriPre<T> &cur, int64_t itc) {
       const int64_t gi = LOWER ? itc : ngrp - 1 - itc;
-      const int64_t r = b0 + TRSV_ROWS * gi + q;
+      const int64_t r = b0 + (int64_t)R * gi + q;
       const int rounds = 1 + __reduce_max_sync(0xffffffffu, (unsigned)cur.rnd);
       for (int rd = 0; rd < rounds; rd++) {
         const bool active = (cur.rnd == rd);
@@ -475,23 +481,23 @@ __device__ __forceinline__ void trsv_block(const TriEll<T> &M, T *x, int64_t npa
           v[k] = T(0);
           if (c[k] >= 0) v[k] = trsv_peek(S, c[k]);
         }
-        trsv_wait<TRSV_EPL, T>(S, c, v, st, spin_ns);
+        trsv_wait<TRSV_EPL, T>(S, c, v, st, spin_ns, poll_ns);
         T acc = T(0);
 #pragma unroll
         for (int k = 0; k < TRSV_EPL; k++)
           if (c[k] >= 0) acc += cur.a[k] * v[k];
-        // entries beyond the first 16 of a row; the trip count
-        // (wd - 16) / TRSV_LANES is the same for every lane
+        // entries beyond the first TRSV_EPL * lanes of a row, one per lane
+        // and step; every lane takes the same number of steps
         const int64_t e = base + (r - b0) * wd;
-        for (int k = g + 16; k < wd; k += TRSV_LANES) {
-          int ce[1] = {active ? __ldg(M.col + e + k) : -1};
+        for (int k0 = TRSV_EPL * lanes; k0 < wd; k0 += lanes) {
+          const int k = k0 + g;
+          int ce[1] = {(active && k < wd) ? __ldg(M.col + e + k) : -1};
           T ve[1] = {T(0)};
           if (ce[0] >= 0) ve[0] = trsv_peek(S, ce[0]);
-          trsv_wait<1, T>(S, ce, ve, st, spin_ns);
+          trsv_wait<1, T>(S, ce, ve, st, spin_ns, poll_ns);
           if (ce[0] >= 0) acc += __ldg(M.val + e + k) * ve[0];
         }
-#pragma unroll
-        for (int o = TRSV_LANES / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        for (int o = lanes / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
         if (active && g == 0) {
           const T val = (cur.rhs - acc) * cur.rdg;
           stage[r - b0] = val;
@@ -503,14 +509,14 @@ __device__ __forceinline__ void trsv_block(const TriEll<T> &M, T *x, int64_t npa
     // two descriptor sets used in turn: the next group's entries load while
     // this one waits, and no register copy waits for those loads
     TriPre<T> p0, p1;
-    trsv_fetch<LOWER, T>(M, b0, base, wd, ngrp, it, q, g, rhs_of, p0);
+    trsv_fetch<LOWER, T>(M, b0, base, wd, ngrp, it, q, g, lanes, rhs_of, p0);
     for (;;) {
       const int64_t it1 = it + twarps;
-      if (it1 < ngrp) trsv_fetch<LOWER, T>(M, b0, base, wd, ngrp, it1, q, g, rhs_of, p1);
+      if (it1 < ngrp) trsv_fetch<LOWER, T>(M, b0, base, wd, ngrp, it1, q, g, lanes, rhs_of, p1);
       process(p0, it);
       if (it1 >= ngrp) break;
       const int64_t it2 = it1 + twarps;
-      if (it2 < ngrp) trsv_fetch<LOWER, T>(M, b0, base, wd, ngrp, it2, q, g, rhs_of, p0);
+      if (it2 < ngrp) trsv_fetch<LOWER, T>(M, b0, base, wd, ngrp, it2, q, g, lanes, rhs_of, p0);
       process(p1, it1);
       if (it2 >= ngrp) break;
       it = it2;
@@ -594,7 +600,7 @@ __device__ __forceinline__ void chain_fetch(const TriChain<T> &M, const TriSrc<T
 
 template <bool LOWER, typename T, typename RHS>
 __device__ __forceinline__ void trsv_chain(const TriChain<T> &M, T *x, int64_t npad, int64_t bsize, long long spin_ns,
-                                           State *st, T *stage_mem, RHS rhs_of) {
+                                           int poll_ns, State *st, T *stage_mem, RHS rhs_of) {
   const int64_t b0 = (int64_t)grank() * bsize;
   const int64_t b1 = min(npad, b0 + bsize);
   const int64_t nb = b1 > b0 ? b1 - b0 : 0;
@@ -616,7 +622,7 @@ __device__ __forceinline__ void trsv_chain(const TriChain<T> &M, T *x, int64_t n
       const int cnt = cur.meta & 7;
       const int64_t r = LOWER ? (int64_t)cur.r0 + q : (int64_t)cur.r0 - q;
       const bool active = q < cnt;
-      trsv_wait<TRSV_EPL, T>(S, cur.c, cur.v, st, spin_ns);
+      trsv_wait<TRSV_EPL, T>(S, cur.c, cur.v, st, spin_ns, poll_ns);
       T acc = T(0), cf[TRSV_ROWS];
 #pragma unroll
       for (int d = 0; d < TRSV_ROWS; d++) cf[d] = T(0);
@@ -634,7 +640,7 @@ __device__ __forceinline__ void trsv_chain(const TriChain<T> &M, T *x, int64_t n
         int ce[1] = {active ? __ldg(M.col + e + k) : -1};
         T ve[1] = {T(0)};
         if (ce[0] >= 0) ve[0] = trsv_peek(S, ce[0]);
-        trsv_wait<1, T>(S, ce, ve, st, spin_ns);
+        trsv_wait<1, T>(S, ce, ve, st, spin_ns, poll_ns);
         if (ce[0] >= 0) acc += __ldg(M.val + e + k) * ve[0];
       }
 #pragma unroll

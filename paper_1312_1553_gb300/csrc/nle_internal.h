@@ -100,6 +100,7 @@ struct Opts {
   int recompute;
   long long spin_ns;
   int trsv_warps;     // warps per CTA that take part in the triangular solves
+  int poll_ns;        // pause between two polls of a triangular-solve wait (0: none)
   int bfgs_full;      // 1: pairs (s_k, r_k - r_{k+1}) (full BFGS update), 0: (s_k, r_k)
 };
 
@@ -121,6 +122,7 @@ struct Dev {
   const T *Lval = nullptr, *Uval = nullptr;
   const T *rdiag = nullptr;  // reciprocal diagonal of L (1 on padding rows)
   const uint8_t *Lround = nullptr, *Uround = nullptr;
+  int trows = TRSV_ROWS;  // level schedule: rows a warp takes at a time (4, or 2 for wide rows)
   // chain schedule (chain = 1): the device order is the factored matrix's
   // own row order, and each slab's rows are solved as per-warp task lists
   // (Lwp/Uwp: NWARP + 1 offsets per slab into Ltask/Utask, a task = {first

@@ -232,7 +232,7 @@ constexpr bool kChainTU = NLE_CHAIN_TU != 0;
 
 template <typename T>
 __device__ __forceinline__ void trsv_forward(const Dev<T> &D, Shared &sh, const Ctl &ctl, int k) {
-  const TriEll<T> L{D.Loff, D.Lw, D.Lcol, D.Lval, D.rdiag, D.Lround};
+  const TriEll<T> L{D.Loff, D.Lw, D.Lcol, D.Lval, D.rdiag, D.Lround, D.trows};
   T *bufA = reinterpret_cast<T *>(nle_dyn_smem);
   T *bufB = bufA + D.bsize;
   const int64_t b0 = (int64_t)grank() * D.bsize;
@@ -246,9 +246,10 @@ __device__ __forceinline__ void trsv_forward(const Dev<T> &D, Shared &sh, const 
   }
   if constexpr (kChainTU) {
     const TriChain<T> C{D.Loff, D.Lw, D.Lcol, D.Lval, D.rdiag, D.Lwp, D.Ltask};
-    trsv_chain<true, T>(C, D.z, D.npad, D.bsize, ctl.spin_ns, D.st, bufA, [&](int64_t r) { return bufB[r - b0]; });
+    trsv_chain<true, T>(C, D.z, D.npad, D.bsize, ctl.spin_ns, ctl.poll_ns, D.st, bufA,
+                        [&](int64_t r) { return bufB[r - b0]; });
   } else {
-    trsv_block<true, T>(L, D.z, D.npad, D.bsize, ctl.twarps, ctl.spin_ns, D.st, bufA,
+    trsv_block<true, T>(L, D.z, D.npad, D.bsize, ctl.twarps, ctl.spin_ns, ctl.poll_ns, D.st, bufA,
                         [&](int64_t r) { return bufB[r - b0]; });
   }
 }
@@ -258,15 +259,16 @@ __device__ __forceinline__ void trsv_forward(const Dev<T> &D, Shared &sh, const 
 // __syncthreads, so no grid barrier separates the two solves.
 template <typename T>
 __device__ __forceinline__ void trsv_backward(const Dev<T> &D, const Ctl &ctl) {
-  const TriEll<T> U{D.Uoff, D.Uw, D.Ucol, D.Uval, D.rdiag, D.Uround};
+  const TriEll<T> U{D.Uoff, D.Uw, D.Ucol, D.Uval, D.rdiag, D.Uround, D.trows};
   const T *bufA = reinterpret_cast<const T *>(nle_dyn_smem);
   T *bufB = reinterpret_cast<T *>(nle_dyn_smem) + D.bsize;
   const int64_t b0 = (int64_t)grank() * D.bsize;
   if constexpr (kChainTU) {
     const TriChain<T> C{D.Uoff, D.Uw, D.Ucol, D.Uval, D.rdiag, D.Uwp, D.Utask};
-    trsv_chain<false, T>(C, D.c0, D.npad, D.bsize, ctl.spin_ns, D.st, bufB, [&](int64_t r) { return bufA[r - b0]; });
+    trsv_chain<false, T>(C, D.c0, D.npad, D.bsize, ctl.spin_ns, ctl.poll_ns, D.st, bufB,
+                         [&](int64_t r) { return bufA[r - b0]; });
   } else {
-    trsv_block<false, T>(U, D.c0, D.npad, D.bsize, ctl.twarps, ctl.spin_ns, D.st, bufB,
+    trsv_block<false, T>(U, D.c0, D.npad, D.bsize, ctl.twarps, ctl.spin_ns, ctl.poll_ns, D.st, bufB,
                          [&](int64_t r) { return bufA[r - b0]; });
   }
 }
@@ -631,6 +633,7 @@ __device__ void load_state(const Dev<T> &D, Shared &sh, Ctl &ctl, const Opts &O,
   ctl.rbuf = 0;
   ctl.spin_ns = O.spin_ns;
   ctl.twarps = max(1, min(NWARP, O.trsv_warps));
+  ctl.poll_ns = O.poll_ns;
   if (threadIdx.x == 0) {
     sh.ok = 1;
     for (int s = 0; s < KMAX; s++) sh.order[s] = s;

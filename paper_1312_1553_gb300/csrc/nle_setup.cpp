@@ -340,13 +340,13 @@ static void pack(int64_t n, int64_t npad, int H, const std::vector<int64_t> &rp,
 }
 
 // Per-slab ELL of a strictly triangular matrix given by rows (relabelled
-// order), plus the round of every row inside its group of TRSV_ROWS rows: the length
+// order), plus the round of every row inside its group of R rows: the length
 // of the longest dependency chain ending at the row within the group
 // (lower: earlier rows of the group; upper: later rows).
 template <typename TV>
 static void ell(int64_t n, int64_t npad, int64_t bsize, bool lower, const std::vector<int64_t> &rp,
                 const std::vector<int32_t> &col, const std::vector<double> &val, const std::vector<int32_t> *lev,
-                EllHost<TV> &out) {
+                int R, EllHost<TV> &out) {
   const int64_t ns = (npad + bsize - 1) / bsize;
   out.off.assign(ns + 1, 0);
   out.width.assign(ns, 8);
@@ -369,8 +369,8 @@ static void ell(int64_t n, int64_t npad, int64_t bsize, bool lower, const std::v
       }
     }
   out.round.assign(npad, 0);
-  for (int64_t g0 = 0; g0 < n; g0 += TRSV_ROWS) {
-    const int64_t g1 = std::min(n, g0 + TRSV_ROWS);
+  for (int64_t g0 = 0; g0 < n; g0 += R) {
+    const int64_t g1 = std::min(n, g0 + R);
     if (lev) {
       // one level per round: rank of the row's level among the group's
       // levels, ascending for L, descending for L^T
@@ -397,18 +397,18 @@ static void ell(int64_t n, int64_t npad, int64_t bsize, bool lower, const std::v
 }
 
 template <typename TV>
-void build_sell(const Permuted &P, int H, int64_t bsize, bool level_rounds, SellSet<TV> &S) {
+void build_sell(const Permuted &P, int H, int64_t bsize, bool level_rounds, int R, SellSet<TV> &S) {
   pack<TV>(P.n, P.npad, H, P.Arp, P.Acol, P.Aval, 0, 0, S.A);
   pack<double>(P.n, P.npad, H, P.Arp, P.Acol, P.Aval, 0, 0, S.A64);
   const std::vector<int32_t> *lev = level_rounds ? &P.lev : nullptr;
-  ell<TV>(P.n, P.npad, bsize, true, P.Lrp, P.Lcol, P.Lval, lev, S.L);
-  ell<TV>(P.n, P.npad, bsize, false, P.Urp, P.Ucol, P.Uval, lev, S.U);
+  ell<TV>(P.n, P.npad, bsize, true, P.Lrp, P.Lcol, P.Lval, lev, R, S.L);
+  ell<TV>(P.n, P.npad, bsize, false, P.Urp, P.Ucol, P.Uval, lev, R, S.U);
   S.diag.assign(P.npad, TV(1));
   for (int64_t i = 0; i < P.n; i++) S.diag[i] = TV(1.0 / P.diag[i]);  // reciprocal pivots
 }
 
-template void build_sell<float>(const Permuted &, int, int64_t, bool, SellSet<float> &);
-template void build_sell<double>(const Permuted &, int, int64_t, bool, SellSet<double> &);
+template void build_sell<float>(const Permuted &, int, int64_t, bool, int, SellSet<float> &);
+template void build_sell<double>(const Permuted &, int, int64_t, bool, int, SellSet<double> &);
 
 template <typename TV>
 void build_chain(const Permuted &P, int64_t bsize, bool lower, int nwarps, ChainHost<TV> &out) {

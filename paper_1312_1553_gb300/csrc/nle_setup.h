@@ -96,10 +96,11 @@ void slab_level_order(const Factor &F, int64_t bsize, const int32_t *locality, s
 void permute(int64_t n, const int64_t *rp, const int32_t *ci, const double *va, const Factor &F,
              const std::vector<int32_t> &perm, const std::vector<int32_t> &iperm, int64_t npad, Permuted &P);
 
-// level_rounds: split every group of TRSV_ROWS rows into one round per level (needed
-// when dependencies can point to later slabs; see trsv_block).
+// level_rounds: split every group of R rows (the rows a warp of the level
+// schedule takes at a time, 4 or 2) into one round per level (needed when
+// dependencies can point to later slabs; see trsv_block).
 template <typename TV>
-void build_sell(const Permuted &P, int H, int64_t bsize, bool level_rounds, SellSet<TV> &S);
+void build_sell(const Permuted &P, int H, int64_t bsize, bool level_rounds, int R, SellSet<TV> &S);
 
 // Chain schedule of the strictly lower (lower = true: P.Lrp/Lcol/Lval, levels
 // P.lev) or upper (P.Urp/Ucol/Uval, levels P.levU) factor for nwarps warps

@@ -43,7 +43,8 @@ class nle_options(ctypes.Structure):
                 ("max_dacg", ctypes.c_int), ("precision", ctypes.c_int), ("exit_eigres", ctypes.c_int),
                 ("exit_stagnation", ctypes.c_int), ("dacg_recompute", ctypes.c_int),
                 ("spin_timeout_s", ctypes.c_double), ("grid_ctas", ctypes.c_int), ("trsv_warps", ctypes.c_int),
-                ("ordering", ctypes.c_int), ("bfgs_update", ctypes.c_int), ("trsv_schedule", ctypes.c_int)]
+                ("ordering", ctypes.c_int), ("bfgs_update", ctypes.c_int), ("trsv_schedule", ctypes.c_int),
+                ("trsv_poll_ns", ctypes.c_int), ("trsv_rows", ctypes.c_int)]
 
 
 class nle_stats(ctypes.Structure):
@@ -56,7 +57,8 @@ class nle_stats(ctypes.Structure):
                 ("dacg_iterations", ctypes.c_int64), ("dacg_sum_m", ctypes.c_int64),
                 ("kernel_launches", ctypes.c_int64), ("ms_phase", ctypes.c_double * 8), ("ascending", ctypes.c_int),
                 ("ms_batch", ctypes.c_double), ("trsv_schedule", ctypes.c_int), ("tune_ms_level", ctypes.c_double),
-                ("tune_ms_chain", ctypes.c_double), ("strands", ctypes.c_int64)]
+                ("tune_ms_chain", ctypes.c_double), ("tune_ms_level2", ctypes.c_double), ("strands", ctypes.c_int64),
+                ("trsv_rows", ctypes.c_int)]
 
 
 class nle_pcg_info(ctypes.Structure):
@@ -370,7 +372,8 @@ def stats_dict(s: nle_stats) -> dict:
                 kernel_launches=int(s.kernel_launches),
                 ms_phase=dict(zip(PHASES, [float(x) for x in s.ms_phase])), ascending=bool(s.ascending),
                 ms_batch=float(s.ms_batch), trsv_schedule=SCHEDULES.get(int(s.trsv_schedule), "none"),
-                tune_ms=dict(level=float(s.tune_ms_level), chain=float(s.tune_ms_chain)), strands=int(s.strands))
+                tune_ms=dict(level=float(s.tune_ms_level), chain=float(s.tune_ms_chain),
+                             level2=float(s.tune_ms_level2)), strands=int(s.strands), trsv_rows=int(s.trsv_rows))
 
 
 def _eigsh_function():

@@ -43,7 +43,7 @@ def test_default_options(lib):
     o = nle.nle_default_options()
     assert o.k_max == 5 and o.tau_pcg == 1e-2 and o.tau_dacg == 1e-2 and o.max_dacg == 5000
     assert o.precision == nle.NLE_FP64 and o.exit_eigres == 1 and o.exit_stagnation == 1
-    assert o.trsv_schedule == nle.NLE_SCHED_AUTO and o.trsv_warps == 16
+    assert o.trsv_schedule == nle.NLE_SCHED_AUTO and o.trsv_warps == 16 and o.trsv_rows == 0 and o.trsv_poll_ns == 0
 
 
 def _create(A, opt=None):

@@ -420,14 +420,16 @@ def test_solve_full_size_hex27_96(nle):
     gk = gk.numpy().ravel()
     elems = np.array(gold["grad_elems"])
     ref = np.array(gold["grad_kappa"])
-    # each term v_j v_j^T is off by at most twice its eigenvector's angle
-    # (bounded above); the sum over the pairs by their sum
-    gtol = 2 * float(np.sum(bnd))
+    # the gradient of sum lambda_j is the trace of dA against the spectral
+    # projector V V^T of all p pairs, which does not depend on how the pairs
+    # of a cluster are rotated inside it: it is held to the stated gradient
+    # tolerance, relative 1e-6 (the per-pair angle bounds, summed, would
+    # allow 2 sum(bnd))
     gerr = np.linalg.norm(gk[elems] - ref) / np.linalg.norm(ref)
-    print(f"element gradient: relative error {gerr:.2e} (bound {gtol:.2e}), "
+    print(f"element gradient: relative error {gerr:.2e} (per-pair bound {2 * float(np.sum(bnd)):.2e}), "
           f"norm {np.linalg.norm(gk):.6e} vs {gold['grad_kappa_norm']:.6e}")
-    assert gerr <= gtol, (gerr, gtol)
-    assert abs(np.linalg.norm(gk) - gold["grad_kappa_norm"]) <= gtol * gold["grad_kappa_norm"]
+    assert gerr <= 1e-6, gerr
+    assert abs(np.linalg.norm(gk) - gold["grad_kappa_norm"]) <= 1e-6 * gold["grad_kappa_norm"]
     assert abs(float(A.meta["kappa"].ravel() @ gk) - lam.sum()) <= 1e-9 * lam.sum()
 
 

@@ -1,5 +1,6 @@
-"""The two schedules of the triangular solves (nle_options.trsv_schedule)
-and the autotuner that picks between them, against the oracle.
+"""The schedules of the triangular solves (nle_options.trsv_schedule, and
+the rows per warp step of the level schedule, nle_options.trsv_rows) and the
+autotuner that picks between them, against the oracle.
 
 Both schedules apply the same (L L^T)^{-1} of Section 2 (only the order in
 which warps take the rows differs), so each is held to the oracle's P0hat
@@ -16,7 +17,7 @@ from oracle.solver import p0hat
 
 pytestmark = pytest.mark.gpu
 PRECS = ["fp64", "mixed"]
-SCHEDS = ["level", "chain"]
+SCHEDS = ["level", "level2", "chain"]
 NAMES = ["aniso2d_30x37", "diff3d7_24", "diff2d5_60x70", "hex27_16", "rgg3000"]
 
 
@@ -39,9 +40,12 @@ def load(name):
 
 
 def solver(nle, A, prec, sched, **opts):
+    """sched: auto, level (4 rows per warp step), level2 (2 rows), chain."""
     o = dict(precision=nle.NLE_MIXED if prec == "mixed" else nle.NLE_FP64,
-             trsv_schedule={"auto": nle.NLE_SCHED_AUTO, "level": nle.NLE_SCHED_LEVEL,
+             trsv_schedule={"auto": nle.NLE_SCHED_AUTO, "level": nle.NLE_SCHED_LEVEL, "level2": nle.NLE_SCHED_LEVEL,
                             "chain": nle.NLE_SCHED_CHAIN}[sched])
+    if sched == "level2":
+        o["trsv_rows"] = 2
     o.update(opts)
     return nle.Eigensolver(A, o)
 
@@ -82,7 +86,9 @@ def test_solve_matches_oracle_with_schedule(nle, name, sched, prec):
     s.factor_ic(st["lfil"], st["tau_ic"])
     lam, V, stats = s.solve(p, st["tol"], 100, 20, X0)
     s.close()
-    assert stats["trsv_schedule"] == sched
+    assert stats["trsv_schedule"] == ("level" if sched == "level2" else sched)
+    if sched != "chain":
+        assert stats["trsv_rows"] == (2 if sched == "level2" else 4)
     lam = lam.cpu().numpy()
     V = V.cpu().numpy()
     lref, Vref, _ = O.dacg_newton(A, p, X0, O.OracleOptions(tol=st["tol"], lfil=st["lfil"], tau_ic=st["tau_ic"]))
@@ -102,14 +108,17 @@ def test_autotuner_times_both_and_keeps_the_faster(nle):
     lam, V, stats = s.solve(2, 1e-8, 100, 20, W.start_vectors(A.n, 2, 1))
     s.close()
     t = stats["tune_ms"]
-    assert t["level"] > 0 and t["chain"] > 0
-    assert stats["trsv_schedule"] == ("chain" if t["chain"] < t["level"] else "level")
+    assert t["level"] > 0 and t["chain"] > 0 and t["level2"] > 0
+    best = min(t, key=t.get)
+    assert stats["trsv_schedule"] == ("chain" if best == "chain" else "level")
+    if best != "chain":
+        assert stats["trsv_rows"] == (2 if best == "level2" else 4)
     assert all(stats["converged"])
     s = solver(nle, A, "mixed", "auto", ordering=nle.NLE_ORDER_MULTICOLOR1)
     s.factor_ic(st["lfil"], st["tau_ic"])
     lam, V, stats = s.solve(2, 1e-8, 100, 20, W.start_vectors(A.n, 2, 1))
     s.close()
-    assert stats["trsv_schedule"] == "level" and stats["tune_ms"]["chain"] == 0
+    assert stats["trsv_schedule"] == "level" and stats["tune_ms"]["chain"] == 0 and stats["tune_ms"]["level2"] > 0
     with pytest.raises(nle.NLEError) as e:
         s = solver(nle, A, "mixed", "chain", ordering=nle.NLE_ORDER_MULTICOLOR1)
         s.factor_ic(st["lfil"], st["tau_ic"])
