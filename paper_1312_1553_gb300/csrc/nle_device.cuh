@@ -71,6 +71,32 @@ __device__ __forceinline__ void ldr(const int32_t *p, int (&o)[2]) {
   o[0] = v.x, o[1] = v.y;
 }
 
+// Read-only loads issued exactly where they are written: the descriptor
+// loads of the triangular solves are meant to be in flight while the warp
+// works on the previous group, and a plain read-only load may be sunk by the
+// compiler down to its first use, which puts its latency back on the
+// dependency chain.
+__device__ __forceinline__ int ld_pinned(const int32_t *p) {
+  int v;
+  asm volatile("ld.global.nc.s32 %0, [%1];" : "=r"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ float ld_pinned(const float *p) {
+  float v;
+  asm volatile("ld.global.nc.f32 %0, [%1];" : "=f"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ double ld_pinned(const double *p) {
+  double v;
+  asm volatile("ld.global.nc.f64 %0, [%1];" : "=d"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ int ld_pinned(const uint8_t *p) {
+  unsigned short v;
+  asm volatile("ld.global.nc.u8 %0, [%1];" : "=h"(v) : "l"(p));
+  return (int)v;
+}
+
 // ---------------------------------------------------------------------------
 // memory-model helpers (PTX): relaxed gpu-scope loads/stores bypass L1 and
 // observe other SMs' stores; acquire/release for the grid barrier.
@@ -354,7 +380,8 @@ struct TriEll {
   const int32_t *col;    // -1 = padding
   const T *val;
   const T *rdiag;         // npad: reciprocal pivots 1 / L_rr
-  const uint8_t *round;   // npad: round of the row inside its group of rows
+  const uint8_t *round;   // npad: round of the row inside its group of rows (low nibble) and
+                          // the group's last round (high nibble)
   int rows;               // rows a warp takes at a time: 4 (8 lanes per row) or 2 (16 lanes)
 };
 
@@ -377,16 +404,16 @@ __device__ __forceinline__ void trsv_fetch(const TriEll<T> &M, int64_t b0, int64
     P.c[k] = -1;
     P.a[k] = T(0);
     if (g + k * lanes < wd) {
-      P.c[k] = __ldg(M.col + e + k * lanes);
-      P.a[k] = __ldg(M.val + e + k * lanes);
+      P.c[k] = ld_pinned(M.col + e + k * lanes);
+      P.a[k] = ld_pinned(M.val + e + k * lanes);
     }
   }
-  P.rnd = __ldg(M.round + r);
+  P.rnd = ld_pinned(M.round + r);
   P.rhs = T(0);
   P.rdg = T(1);
   if (g == 0) {
     P.rhs = rhs_of(r);
-    P.rdg = __ldg(M.rdiag + r);
+    P.rdg = ld_pinned(M.rdiag + r);
   }
 }
 
@@ -470,9 +497,9 @@ __device__ __forceinline__ void trsv_block(const TriEll<T> &M, T *x, int64_t npa
     auto process = [&](const TriPre<T> &cur, int64_t itc) {
       const int64_t gi = LOWER ? itc : ngrp - 1 - itc;
       const int64_t r = b0 + (int64_t)R * gi + q;
-      const int rounds = 1 + __reduce_max_sync(0xffffffffu, (unsigned)cur.rnd);
+      const int rounds = 1 + (cur.rnd >> 4);  // the same in every lane of the group
       for (int rd = 0; rd < rounds; rd++) {
-        const bool active = (cur.rnd == rd);
+        const bool active = ((cur.rnd & 15) == rd);
         int c[TRSV_EPL];
         T v[TRSV_EPL];
 #pragma unroll
@@ -573,7 +600,7 @@ struct ChainPre {
 template <bool LOWER, typename T, typename RHS>
 __device__ __forceinline__ void chain_fetch(const TriChain<T> &M, const TriSrc<T> &S, int64_t b0, int64_t base, int wd,
                                             int ti, int q, int g, RHS &rhs_of, ChainPre<T> &P) {
-  const int2 tk = __ldg(M.task + ti);
+  const int2 tk = make_int2(ld_pinned(&M.task[ti].x), ld_pinned(&M.task[ti].y));
   P.r0 = tk.x;
   P.meta = tk.y;
   const bool active = q < (tk.y & 7);
@@ -584,8 +611,8 @@ __device__ __forceinline__ void chain_fetch(const TriChain<T> &M, const TriSrc<T
     P.c[k] = -1;
     P.a[k] = T(0);
     if (active && g + k * TRSV_LANES < wd) {
-      P.c[k] = __ldg(M.col + e + k * TRSV_LANES);
-      P.a[k] = __ldg(M.val + e + k * TRSV_LANES);
+      P.c[k] = ld_pinned(M.col + e + k * TRSV_LANES);
+      P.a[k] = ld_pinned(M.val + e + k * TRSV_LANES);
     }
   }
 #pragma unroll
@@ -594,7 +621,7 @@ __device__ __forceinline__ void chain_fetch(const TriChain<T> &M, const TriSrc<T
   P.rdg = T(1);
   if (active) {
     P.rhs = rhs_of(r);
-    P.rdg = __ldg(M.rdiag + r);
+    P.rdg = ld_pinned(M.rdiag + r);
   }
 }
 

@@ -340,7 +340,8 @@ static void pack(int64_t n, int64_t npad, int H, const std::vector<int64_t> &rp,
 }
 
 // Per-slab ELL of a strictly triangular matrix given by rows (relabelled
-// order), plus the round of every row inside its group of R rows: the length
+// order), plus the round of every row inside its group of R rows (low
+// nibble; the group's last round in the high nibble): the length
 // of the longest dependency chain ending at the row within the group
 // (lower: earlier rows of the group; upper: later rows).
 template <typename TV>
@@ -393,6 +394,13 @@ static void ell(int64_t n, int64_t npad, int64_t bsize, bool lower, const std::v
         for (int64_t e = rp[r]; e < rp[r + 1]; e++)
           if (col[e] < g1) out.round[r] = std::max<uint8_t>(out.round[r], out.round[col[e]] + 1);
     }
+    // every row also carries the number of rounds of its group, less one,
+    // in the high nibble (rounds <= R <= 4), so a warp needs no reduction
+    // to learn it
+    // (padding rows past n included: every lane of the group must agree)
+    uint8_t last = 0;
+    for (int64_t r = g0; r < g1; r++) last = std::max(last, out.round[r]);
+    for (int64_t r = g0; r < std::min(npad, g0 + R); r++) out.round[r] = (uint8_t)(out.round[r] | (last << 4));
   }
 }
 

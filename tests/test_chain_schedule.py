@@ -229,9 +229,10 @@ def simulate_level(E, n, bsize, R, rhs_dev, lower, nwarps=NWARP):
                 rows = [qd["b0"] + R * gi + q for q in range(R)]
                 s = qd["s"]
                 wd = E["width"][s]
-                rounds = 1 + max(int(E["round"][r]) for r in rows)
+                rounds = 1 + max(int(E["round"][r]) & 15 for r in rows)
+                assert all(1 + (int(E["round"][r]) >> 4) == rounds for r in rows)
                 rd = qd["rnd"]
-                act = [r for r in rows if E["round"][r] == rd]
+                act = [r for r in rows if (int(E["round"][r]) & 15) == rd]
                 ready = True
                 for r in act:
                     e = E["off"][s] + (r - qd["b0"]) * wd
