@@ -66,6 +66,7 @@ def parse():
                     help="outer step cap; 0 = the workload's (the paper's ITMAX = 100; 400 for workloads with "
                          "eigenvalue clusters)")
     ap.add_argument("--spin-timeout", type=float, default=0.0, help="0 = library default (seconds)")
+    ap.add_argument("--batch-ctas", type=int, default=0, help="graph batch: CTAs per problem (0: 4 mixed, 8 FP64)")
     ap.add_argument("--schedule", default="auto", choices=["auto", "level", "chain"],
                     help="schedule of the triangular solves (auto = timed at set-up, the faster kept)")
     ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
@@ -346,8 +347,9 @@ def batch_main(args, world, rank, local, cpu):
         solvers = []
         for A in mats:
             # FP64 needs 8 CTAs per problem for the largest graphs (n = 60,000)
-            s = nle.Eigensolver(A, dict(precision=prec, grid_ctas=4 if prec == nle.NLE_MIXED else 8,
-                                        trsv_schedule=nle.NLE_SCHED_LEVEL), stream=stream)
+            ctas = args.batch_ctas or (4 if prec == nle.NLE_MIXED else 8)
+            s = nle.Eigensolver(A, dict(precision=prec, grid_ctas=ctas, trsv_schedule=nle.NLE_SCHED_LEVEL),
+                                stream=stream)
             s.factor_ic(30, 1e-2)
             solvers.append(s)
         ic_seconds = time.perf_counter() - t0
@@ -422,7 +424,8 @@ def batch_main(args, world, rank, local, cpu):
                                      f"n ~ U[2000, 60000], p = {BATCH_P}",
                             n_total=sum(A.n for A in mats), nnz_total=sum(A.nnz for A in mats), lfil=30, tau_ic=1e-2,
                             tol=1e-8, ic_seconds=ic_seconds, l2="working set > 129 MB L2 (no flush needed)",
-                            parallelism=f"replicas{world}" if world > 1 else f"single GPU, groups of {4 if prec == nle.NLE_MIXED else 8} CTAs"),
+                            parallelism=f"replicas{world}" if world > 1 else
+                            f"single GPU, groups of {args.batch_ctas or (4 if prec == nle.NLE_MIXED else 8)} CTAs"),
                 roofline=dict(bound="hbm", achieved=achieved, peak=peak, unit="GB/s", frac=achieved / peak,
                               traffic=load_traffic("k_batch", BATCH), kernel="k_batch",
                               peak_source=f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)" if peak_kind == "measured"
