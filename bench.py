@@ -49,9 +49,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default=None, choices=["mixed", "fp64"],
-                    help="default: mixed, FP64 for the graph batch (its lambda_2/lambda_3 clusters are too tight "
-                         "for FP32 inner solves)")
+    ap.add_argument("--precision", default=None, choices=["mixed", "fp64"], help="default: mixed")
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 arm (profiling runs)")
@@ -106,7 +104,7 @@ BATCH_MAX_NEWTON = 400
 def batch_problem_start(A, b: int):
     import workloads as W
 
-    return W.start_vectors(A.n, BATCH_P, W.BASE_SEED + 400 + b)
+    return W.graph_batch_start(A, b, BATCH_P)
 
 
 def cpu_sample_batch() -> dict:
@@ -340,7 +338,7 @@ def batch_main(args, world, rank, local, cpu):
     nle.load_library()
     mats = W.graph_batch(count=256)
     max_newton = args.max_newton or BATCH_MAX_NEWTON
-    prec = nle.NLE_MIXED if args.precision == "mixed" else nle.NLE_FP64  # default FP64 here
+    prec = nle.NLE_FP64 if args.precision == "fp64" else nle.NLE_MIXED
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         t0 = time.perf_counter()
@@ -658,6 +656,7 @@ def main():
                                                     d2h_bytes_per_step=p * A.n * 8 + p * 8),
                 clocks=clocks, gpu_launches=int(sum(x["kernel_launches"] for x in all_stats)),
                 phase_ms=dict(dacg=ms_dacg / args.steps, newton=ms_newton / args.steps),
+                pass_ms={k: sum(x["ms_phase"][k] for x in all_stats) / args.steps for k in nle.PHASES},
                 iterations=dict(pcg=its / args.steps, dacg=dits / args.steps),
                 lambda_first=float(lam_dev[0]), accuracy=accuracy, fp64=fp64,
                 mixed_over_fp64=(value / fp64["value"]) if fp64 else None)

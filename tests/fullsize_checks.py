@@ -52,3 +52,50 @@ def check_eigenvectors(A, V, gold, res_gpu, label):
         print(f"  pair {j + 1:2d}  angle ~ {a:.2e}  bound {b:.2e}")
     assert np.all(ang <= SKETCH_SLACK * bnd), (ang, bnd)
     return ang, bnd
+
+
+def cluster_subspace_angles(A, V, gold, res_gpu, rel_gap=0.02):
+    """Eigenvalue clusters (maximal runs of computed eigenvalues whose
+    consecutive relative gaps are below rel_gap): the distance between the
+    spans of the GPU's and the oracle's eigenvectors of each cluster, as the
+    sketched residual of the best rotation (orthogonal Procrustes) of the
+    oracle's onto the GPU's, and its bound (res_gpu + res_oracle) lambda_max
+    / delta, delta the distance from the cluster to the other computed
+    eigenvalues (the subspace is well conditioned when an individual
+    eigenvector of the cluster is not).  Returns [(pairs, angle, bound)]."""
+    K = gold["sketch_K"]
+    bucket, sign = W.count_sketch_hash(A.n, K, gold["sketch_seed"])
+    glam = np.array(gold["lam"])
+    res_or = np.array(gold["oracle_stats"]["final_res"])
+    p = len(glam)
+    out = []
+    j = 0
+    while j < p:
+        e = j + 1
+        while e < p and (glam[e] - glam[e - 1]) / glam[e] < rel_gap:
+            e += 1
+        if e - j >= 2:
+            idx = list(range(j, e))
+            Yg = np.stack([W.count_sketch(V[i], bucket, sign, K) for i in idx], axis=1)
+            Yo = np.stack([np.array(gold["sketch_V"][i]) for i in idx], axis=1)
+            U, _, Vt = np.linalg.svd(Yo.T @ Yg)
+            ang = float(np.linalg.norm(Yg - Yo @ (U @ Vt)))
+            rest = np.delete(glam, idx)
+            delta = float(np.min(np.abs(rest[:, None] - glam[idx][None, :]))) if len(rest) else np.inf
+            bnd = float(np.sqrt(len(idx)) * max(res_gpu[i] + res_or[i] for i in idx) * glam[e - 1] / delta)
+            out.append(([i + 1 for i in idx], ang, bnd))
+        j = e
+    return out
+
+
+def check_clusters(A, V, gold, res_gpu, label):
+    """Assert each cluster's subspace distance within its bound (sketch
+    slack included) and within 1e-6 wherever that bound allows; print."""
+    rows = cluster_subspace_angles(A, V, gold, res_gpu)
+    print(f"\n{label}: eigenvalue clusters, subspace distance to the oracle's (CountSketch) and its bound")
+    for pairs, a, b in rows:
+        print(f"  pairs {pairs[0]}-{pairs[-1]}  distance ~ {a:.2e}  bound {b:.2e}")
+        assert a <= SKETCH_SLACK * b, (pairs, a, b)
+        if b <= 1e-6:
+            assert a <= 1e-6, (pairs, a)
+    return rows

@@ -83,11 +83,18 @@ def main(names, threads=None, out_dir=HERE):
 
         threadpool_limits(limits=threads, user_api="blas")
     for name in names:
-        A, st = W.workload(name)
+        if name.startswith("graph_batch_"):
+            # problem b of the batched workload, its own start vectors
+            b = int(name.rsplit("_", 1)[1])
+            A = W.graph_batch_problem(b)
+            st = dict(p=4, lfil=30, tau_ic=1e-2, tol=1e-8, max_newton=400, seed=W.BASE_SEED + 400 + b)
+            X0 = W.graph_batch_start(A, b, 4)
+        else:
+            A, st = W.workload(name)
+            X0 = W.start_vectors(A.n, st["p"], st["seed"])
         p = st["p"]
         opt = O.OracleOptions(tol=st["tol"], lfil=st["lfil"], tau_ic=st["tau_ic"],
                               max_newton=st.get("max_newton", 100))
-        X0 = W.start_vectors(A.n, p, st["seed"])
         t0 = time.time()
         lam, V, stats = O.dacg_newton(A, p, X0, opt)
         sec = time.time() - t0
@@ -100,6 +107,8 @@ def main(names, threads=None, out_dir=HERE):
                                                      ("dacg_its", "outer_its", "pcg_its", "converged", "final_res",
                                                       "ascending", "nnz_L", "sigma")},
                    blas_threads=threads)
+        if name.startswith("graph_batch_"):
+            out.update(max_newton=st["max_newton"])
         # CountSketch of every eigenvector (sign convention applied): the
         # full-size tests compare sketches, which estimate ||v_gpu - v_oracle||
         bucket, sign = W.count_sketch_hash(A.n, SKETCH_K, st["seed"])

@@ -367,6 +367,7 @@ def test_solve_full_size_100cubed(nle, prec):
         v = align(V[j, idx], ref)
         assert np.abs(v - ref).max() <= 2e-6
     ang, bnd = FC.check_eigenvectors(A, V, gold, stats["final_res"], f"diff3d7_100 {prec}")
+    FC.check_clusters(A, V, gold, stats["final_res"], f"diff3d7_100 {prec}")
     # the stated eigenvector tolerance, 1e-6, wherever the residual bound
     # allows it
     assert np.all(ang[bnd <= 1e-6] <= 1e-6), ang
@@ -410,6 +411,9 @@ def test_solve_full_size_hex27_96(nle):
         assert np.abs(v - ref).max() <= 10 * st["tol"] * glam[j] / gaps[j], j
     ang, bnd = FC.check_eigenvectors(A, V, gold, stats["final_res"], "hex27_96 mixed")
     assert np.all(ang[bnd <= 1e-6] <= 1e-6), ang
+    # the pairs of a tight cluster are individually ill conditioned; the
+    # span of each cluster is not
+    FC.check_clusters(A, V, gold, stats["final_res"], "hex27_96 mixed")
     _check_solution(A, lam, V, st["tol"])
     assert abs(float(A.val @ grad) - lam.sum()) <= 1e-9 * lam.sum()
     # the backward of sum lambda_j with respect to the element coefficients

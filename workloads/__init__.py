@@ -327,6 +327,18 @@ def graph_batch(count: int = 256, nmin: int = 2000, nmax: int = 60000, seed: int
     return [geometric_graph_laplacian(int(sizes[b]), seed * 1000 + b) for b in range(count)]
 
 
+def graph_batch_problem(b: int, count: int = 256, nmin: int = 2000, nmax: int = 60000,
+                        seed: int = BASE_SEED + 4) -> CSR:
+    """Problem b of graph_batch(count, ...), built alone."""
+    sizes = rng_for(seed).integers(nmin, nmax + 1, size=count)
+    return geometric_graph_laplacian(int(sizes[b]), seed * 1000 + b)
+
+
+def graph_batch_start(A: CSR, b: int, p: int = 4) -> np.ndarray:
+    """Start vectors of problem b of the batched workload (p per problem)."""
+    return start_vectors(A.n, p, BASE_SEED + 400 + b)
+
+
 # ---------------------------------------------------------------------------
 # Workload 5: trilinear hexahedral Poisson stiffness, 27-point
 # ---------------------------------------------------------------------------
