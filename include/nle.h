@@ -107,7 +107,26 @@ typedef struct {
   int trsv_rows;         /* level schedule: rows a warp takes at a time, 4 (8 lanes per row)
                             or 2 (16 lanes, for factors with wide rows); 0 (default): chosen
                             by the autotuner under NLE_SCHED_AUTO, 4 otherwise */
+  int ic_device;         /* where nle_factor_ic computes the numeric factor: NLE_IC_AUTO
+                            (default), NLE_IC_HOST or NLE_IC_DEVICE, see below */
 } nle_options;
+
+/* Where nle_factor_ic computes the numeric IC factor.  Both compute the
+ * same factor bit for bit (same algorithm, same operation order, correctly
+ * rounded operations).
+ *   NLE_IC_HOST    on the host, one column after the other;
+ *   NLE_IC_DEVICE  on the device: one warp per column, columns running
+ *                  concurrently, each waiting (time-bounded) for the
+ *                  earlier columns it depends on; needs lfil <= 31, and a
+ *                  column whose working set outgrows the kernel's per-warp
+ *                  tables (256 candidate rows and columns, 128 entries
+ *                  after the drop test) returns NLE_ERR_ARG;
+ *   NLE_IC_AUTO    the device when lfil <= 31, the host otherwise or when
+ *                  a column outgrows the device tables.
+ * nle_stats reports which ran and how long it took. */
+#define NLE_IC_AUTO 0
+#define NLE_IC_HOST 1
+#define NLE_IC_DEVICE 2
 
 /* Schedule of the triangular solves of Phat_0 = (L L^T)^{-1} (Section 2).
  * Both give the same solution (up to rounding order); they differ in how
@@ -181,6 +200,11 @@ typedef struct {
   double tune_ms_level2;        /*   rows per warp step, chain schedule, level with 2 rows */
   int64_t strands;              /* chain schedule: strands of L (runs of dependent rows) */
   int trsv_rows;                /* level schedule: rows per warp step in use */
+  int ic_on_device;             /* 1 when the IC factor in use was computed on the device */
+  double ms_ic_factor;          /* wall time of the numeric factor (device: with the copies) */
+  double ms_ic_kernel;          /* device time of the factor kernel (0 on the host) */
+  double ms_ic_setup;           /* wall time of the whole nle_factor_ic (factor, levels,
+                                   layouts, autotuner) */
 } nle_stats;
 
 /* Parameters and outcome of one inner solve (nle_pcg). */
@@ -208,8 +232,9 @@ nle_status nle_create(int64_t n, int64_t nnz, const int64_t *rowptr, const int32
 
 /* IC(lfil, tau_IC) factor of A (Section 2: Phat_0 = (L L^T)^{-1}) and the
  * level sets of L and L^T that schedule the triangular solves.
- * The factor is computed on the host in FP64 by a left-looking column
- * algorithm with a fixed operation order: column j starts from the lower
+ * The factor is computed in FP64 (on the device or the host, see
+ * nle_options.ic_device: the same factor bit for bit) by a left-looking
+ * column algorithm with a fixed operation order: column j starts from the lower
  * part of column j of A; for every k < j with L(j,k) != 0, in ascending k,
  * every row i >= j of column k is updated w[i] -= L(i,k) L(j,k); the pivot
  * w[j] must be positive; L(j,j) = sqrt(w[j]), L(i,j) = w[i]/L(j,j); an
@@ -219,8 +244,10 @@ nle_status nle_create(int64_t n, int64_t nnz, const int64_t *rowptr, const int32
  * slab-major, level-minor order of the unknowns (one slab of consecutive
  * rows per CTA, sorted by level of L inside the slab: a relabelling, the
  * method is unchanged).  With nle_options.ordering the factor is that of
- * P A P^T for the multicolour permutation P.  Errors: NLE_ERR_ARG (lfil < 0, tau_IC < 0),
- * NLE_ERR_NOT_SPD (non-positive pivot), NLE_ERR_OOM, NLE_ERR_CUDA.
+ * P A P^T for the multicolour permutation P.  Errors: NLE_ERR_ARG (lfil < 0, tau_IC < 0;
+ * NLE_IC_DEVICE with lfil > 31 or a column beyond the device tables),
+ * NLE_ERR_NOT_SPD (non-positive pivot), NLE_ERR_TIMEOUT (a wait of the device
+ * factor ran past spin_timeout_s), NLE_ERR_OOM, NLE_ERR_CUDA.
  * Calling it again refactors with the new parameters. */
 nle_status nle_factor_ic(nle_t h, int lfil, double tau_ic);
 
@@ -276,8 +303,10 @@ nle_status nle_batch_solve(int count, nle_t *hs, int p, double tol, int max_newt
 
 /* Statistics of the handle's last solve, by nle_solve or as one problem of
  * nle_batch_solve (there the device times of the phases are 0 and ms_batch
- * is the time of the whole batched launch).  NLE_ERR_STATE before any
- * solve. */
+ * is the time of the whole batched launch).  The set-up fields (schedule of
+ * the triangular solves, autotuner timings, IC factor) describe the
+ * handle's current factor and are filled after nle_factor_ic alone (the
+ * solve fields are then 0).  NLE_ERR_STATE before nle_factor_ic. */
 nle_status nle_get_stats(nle_t h, nle_stats *stats);
 
 /* ---- Building blocks of the hot path, exposed for verification ---------- */

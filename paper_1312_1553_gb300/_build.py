@@ -66,9 +66,11 @@ def build(force: bool = False, jobs: int | None = None, verbose: bool = False) -
         cmds.append([nvcc, *NVFLAGS, f"-DNLE_T={typ}", f"-DNLE_RPC={rpc}", f"-DNLE_TAG={tag}",
                      f"-DNLE_CHAIN_TU={chain}", "-c", kern, "-o", o])
         objs.append(o)
-    for src in ("nle_api.cu", "nle_setup.cpp", "nle_noalloc.cu"):
+    for src in ("nle_api.cu", "nle_setup.cpp", "nle_noalloc.cu", "nle_ict.cu"):
         o = os.path.join(BUILD, src.replace(".", "_") + ".o")
-        cmds.append([nvcc, *NVFLAGS, "-c", os.path.join(CSRC, src), "-o", o])
+        # the IC factor must round exactly like the host factor: no contraction
+        extra = ["-fmad=false"] if src == "nle_ict.cu" else []
+        cmds.append([nvcc, *NVFLAGS, *extra, "-c", os.path.join(CSRC, src), "-o", o])
         objs.append(o)
     jobs = jobs or min(len(cmds), max(1, os.cpu_count() or 1))
 

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -13,6 +14,7 @@
 
 #include "../../include/nle.h"
 #include "nle_device.cuh"
+#include "nle_ict.h"
 #include "nle_internal.h"
 #include "nle_setup.h"
 
@@ -194,6 +196,8 @@ struct nle_ctx {
   int trows = TRSV_ROWS;             // level schedule: rows a warp takes at a time (4 or 2)
   double tune_ms[3] = {0.0, 0.0, 0.0};  // measured application time: level (4 rows), chain, level (2 rows)
   int64_t nstrands = 0;
+  int ic_on_device = 0;                         // the factor in use was computed on the device
+  double ic_ms[3] = {0.0, 0.0, 0.0};            // factor (wall), its kernel (device), whole set-up (wall)
   DBuf vecs;   // working-precision vectors
   DBuf vec64;  // Au, r, t
   DBuf dQ, dQt, dS, dR;
@@ -540,6 +544,7 @@ void nle_default_options(nle_options *o) {
   o->trsv_schedule = NLE_SCHED_AUTO;
   o->trsv_poll_ns = 0;
   o->trsv_rows = 0;
+  o->ic_device = NLE_IC_AUTO;
 }
 
 const char *nle_last_error(nle_t h) { return h ? h->err.c_str() : g_create_error.c_str(); }
@@ -574,6 +579,8 @@ nle_status nle_create(int64_t n, int64_t nnz, const int64_t *rowptr, const int32
     return fail(nullptr, NLE_ERR_ARG, "unknown trsv_schedule");
   if (h->opt.trsv_rows != 0 && h->opt.trsv_rows != 2 && h->opt.trsv_rows != 4)
     return fail(nullptr, NLE_ERR_ARG, "trsv_rows must be 0 (tuned), 2 or 4");
+  if (h->opt.ic_device < NLE_IC_AUTO || h->opt.ic_device > NLE_IC_DEVICE)
+    return fail(nullptr, NLE_ERR_ARG, "ic_device must be NLE_IC_AUTO, NLE_IC_HOST or NLE_IC_DEVICE");
   if (h->opt.bfgs_update != NLE_BFGS_SIMPLIFIED && h->opt.bfgs_update != NLE_BFGS_FULL)
     return fail(nullptr, NLE_ERR_ARG, "unknown bfgs_update");
   if (h->opt.bfgs_update == NLE_BFGS_FULL && h->opt.k_max > NLE_MAX_KMAX - 1)
@@ -640,6 +647,77 @@ nle_status nle_multicolor_order(int64_t n, const int64_t *rowptr, const int32_t 
   return NLE_OK;
 }
 
+// IC(lfil, tau_IC) on the device (csrc/nle_ict.cu): the columns of
+// ic_factor_host, bit for bit.  NLE_ERR_NOT_SPD sets *bad; a column that
+// outgrows the kernel's per-warp tables sets *capacity and returns
+// NLE_ERR_ARG.
+static nle_status ic_factor_device(nle_t h, const int64_t *rp, const int32_t *ci, const double *va, int lfil,
+                                   double tau, Factor &F, int64_t *bad, bool *capacity, double *kernel_ms) {
+  const int64_t n = h->n, nnz = rp[n];
+  const int RS = lfil + 1;
+  cudaStream_t st = h->stream;
+  DBuf drp, dci, dva, dcnt, drow, dval, derr;
+  NLE_CUDA(h, dalloc(drp, (size_t)(n + 1) * 8, st));
+  NLE_CUDA(h, dalloc(dci, (size_t)nnz * 4, st));
+  NLE_CUDA(h, dalloc(dva, (size_t)nnz * 8, st));
+  NLE_CUDA(h, cudaMemcpyAsync(drp.p, rp, (size_t)(n + 1) * 8, cudaMemcpyHostToDevice, st));
+  NLE_CUDA(h, cudaMemcpyAsync(dci.p, ci, (size_t)nnz * 4, cudaMemcpyHostToDevice, st));
+  NLE_CUDA(h, cudaMemcpyAsync(dva.p, va, (size_t)nnz * 8, cudaMemcpyHostToDevice, st));
+  NLE_CUDA(h, dalloc(dcnt, (size_t)n * 4, st));
+  NLE_CUDA(h, dalloc(drow, (size_t)n * RS * 4, st));
+  NLE_CUDA(h, dalloc(dval, (size_t)n * RS * 8, st));
+  NLE_CUDA(h, dalloc(derr, sizeof(IctError), st));
+  NLE_CUDA(h, cudaMemsetAsync(dcnt.p, 0xFF, (size_t)n * 4, st));
+  NLE_CUDA(h, cudaMemsetAsync(drow.p, 0xFF, (size_t)n * RS * 4, st));
+  NLE_CUDA(h, cudaMemsetAsync(dval.p, 0xFF, (size_t)n * RS * 8, st));
+  int grid = ict_max_grid(h->nsm);
+  if (grid < 1) return fail(h, NLE_ERR_CUDA, "device IC factor: kernel does not fit on an SM");
+  grid = (int)std::min<int64_t>(grid, (n + ICT_WARPS - 1) / ICT_WARPS);
+  const long long spin_ns = (long long)(h->opt.spin_timeout_s * 1e9);
+  NLE_CUDA(h, cudaEventRecord(h->ev[0], st));
+  NLE_CUDA(h, ict_launch(grid, n, drp.as<int64_t>(), dci.as<int32_t>(), dva.as<double>(), lfil, tau,
+                         dcnt.as<int>(), drow.as<int>(), dval.as<double>(), derr.as<IctError>(), spin_ns, st));
+  NLE_CUDA(h, cudaEventRecord(h->ev[1], st));
+  IctError e{};
+  std::vector<int> cnt(n), row((size_t)n * RS);
+  std::vector<double> val((size_t)n * RS);
+  NLE_CUDA(h, cudaMemcpyAsync(&e, derr.p, sizeof(e), cudaMemcpyDeviceToHost, st));
+  NLE_CUDA(h, cudaMemcpyAsync(cnt.data(), dcnt.p, (size_t)n * 4, cudaMemcpyDeviceToHost, st));
+  NLE_CUDA(h, cudaMemcpyAsync(row.data(), drow.p, (size_t)n * RS * 4, cudaMemcpyDeviceToHost, st));
+  NLE_CUDA(h, cudaMemcpyAsync(val.data(), dval.p, (size_t)n * RS * 8, cudaMemcpyDeviceToHost, st));
+  NLE_CUDA(h, cudaStreamSynchronize(st));
+  float ms = 0.f;
+  NLE_CUDA(h, cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]));
+  *kernel_ms = ms;
+  if (e.code == ICT_ERR_NOT_SPD) {
+    *bad = e.col;
+    return NLE_ERR_NOT_SPD;
+  }
+  if (e.code == ICT_ERR_CAPACITY) {
+    *capacity = true;
+    return fail(h, NLE_ERR_ARG, "device IC factor: column " + std::to_string(e.col) +
+                                    " needs more entries than the kernel's per-warp tables hold");
+  }
+  if (e.code == ICT_ERR_TIMEOUT)
+    return fail(h, NLE_ERR_TIMEOUT, "device IC factor: a wait timed out at column " + std::to_string(e.col));
+  if (e.code != ICT_OK) return fail(h, NLE_ERR_CUDA, "device IC factor: error " + std::to_string(e.code));
+  std::vector<int64_t> cs(n + 1, 0);
+  for (int64_t j = 0; j < n; j++) {
+    if (cnt[j] < 1 || cnt[j] > RS)
+      return fail(h, NLE_ERR_CUDA, "device IC factor: column " + std::to_string(j) + " was not written");
+    cs[j + 1] = cs[j] + cnt[j];
+  }
+  std::vector<int32_t> rows(cs[n]);
+  std::vector<double> vals(cs[n]);
+  for (int64_t j = 0; j < n; j++)
+    for (int t = 0; t < cnt[j]; t++) {
+      rows[cs[j] + t] = row[(size_t)j * RS + t];
+      vals[cs[j] + t] = val[(size_t)j * RS + t];
+    }
+  factor_from_columns(n, std::move(cs), std::move(rows), std::move(vals), F);
+  return NLE_OK;
+}
+
 nle_status nle_factor_ic(nle_t h, int lfil, double tau_ic) {
   if (!h) return fail(nullptr, NLE_ERR_ARG, "NULL handle");
   if (lfil < 0 || !(tau_ic >= 0.0)) return fail(h, NLE_ERR_ARG, "need lfil >= 0 and tau_ic >= 0");
@@ -662,9 +740,30 @@ nle_status nle_factor_ic(nle_t h, int lfil, double tau_ic) {
     ci = bci.data();
     va = bva.data();
   }
+  // the numeric factor: on the device (NLE_IC_DEVICE, or NLE_IC_AUTO when
+  // lfil fits the kernel's column records) or on the host; both give the
+  // same factor bit for bit
+  using clk = std::chrono::steady_clock;
+  const auto t_setup = clk::now();
   Factor F;
-  if (ic_factor_host(h->n, rp, ci, va, lfil, tau_ic, F, &bad) != 0)
+  int icdev = h->opt.ic_device;
+  if (icdev == NLE_IC_DEVICE && lfil > ICT_LFIL_MAX)
+    return fail(h, NLE_ERR_ARG, "the device IC factor needs lfil <= " + std::to_string(ICT_LFIL_MAX));
+  const bool on_dev = icdev == NLE_IC_DEVICE || (icdev == NLE_IC_AUTO && lfil <= ICT_LFIL_MAX);
+  h->ic_on_device = 0;
+  h->ic_ms[0] = h->ic_ms[1] = h->ic_ms[2] = 0.0;
+  bool host = !on_dev;
+  if (on_dev) {
+    bool capacity = false;
+    const nle_status ds = ic_factor_device(h, rp, ci, va, lfil, tau_ic, F, &bad, &capacity, &h->ic_ms[1]);
+    if (ds == NLE_ERR_NOT_SPD) return fail(h, ds, "non-positive pivot in IC column " + std::to_string(bad));
+    if (ds == NLE_OK) h->ic_on_device = 1;
+    else if (capacity && icdev == NLE_IC_AUTO) host = true;  // same factor, computed on the host
+    else return ds;
+  }
+  if (host && ic_factor_host(h->n, rp, ci, va, lfil, tau_ic, F, &bad) != 0)
     return fail(h, NLE_ERR_NOT_SPD, "non-positive pivot in IC column " + std::to_string(bad));
+  h->ic_ms[0] = std::chrono::duration<double, std::milli>(clk::now() - t_setup).count();
   h->F = std::move(F);
   const int H = 32 * h->vw;
   h->npad = ((h->n + H - 1) / H) * H;
@@ -735,6 +834,7 @@ nle_status nle_factor_ic(nle_t h, int lfil, double tau_ic) {
       return s;
   }
   NLE_CUDA(h, cudaStreamSynchronize(h->stream));
+  h->ic_ms[2] = std::chrono::duration<double, std::milli>(clk::now() - t_setup).count();
   h->factored = true;
   return NLE_OK;
 }
@@ -798,6 +898,10 @@ static void schedule_stats(nle_t h, nle_stats *stats) {
   stats->tune_ms_chain = h->tune_ms[1];
   stats->tune_ms_level2 = h->tune_ms[2];
   stats->strands = h->chain ? h->nstrands : 0;
+  stats->ic_on_device = h->ic_on_device;
+  stats->ms_ic_factor = h->ic_ms[0];
+  stats->ms_ic_kernel = h->ic_ms[1];
+  stats->ms_ic_setup = h->ic_ms[2];
 }
 
 template <typename T>
@@ -873,8 +977,11 @@ static nle_status solve_impl(nle_t h, int p, double tol, int max_newton, int max
 
 extern "C" nle_status nle_get_stats(nle_t h, nle_stats *stats) {
   if (!h || !stats) return fail(h, NLE_ERR_ARG, "NULL argument");
-  if (!h->has_stats) return fail(h, NLE_ERR_STATE, "no solve has run on this handle");
-  *stats = h->last_stats;
+  if (!h->has_stats && !h->factored) return fail(h, NLE_ERR_STATE, "neither a factor nor a solve on this handle");
+  nle_stats out{};
+  if (h->has_stats) out = h->last_stats;
+  if (h->factored) schedule_stats(h, &out);
+  *stats = out;
   return NLE_OK;
 }
 

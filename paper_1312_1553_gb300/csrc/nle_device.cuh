@@ -72,10 +72,11 @@ __device__ __forceinline__ void ldr(const int32_t *p, int (&o)[2]) {
 }
 
 // Read-only loads issued exactly where they are written: the descriptor
-// loads of the triangular solves are meant to be in flight while the warp
-// works on the previous group, and a plain read-only load may be sunk by the
+// loads of the chain schedule are meant to be in flight while the warp works
+// on the previous task, and a plain read-only load may be sunk by the
 // compiler down to its first use, which puts its latency back on the
-// dependency chain.
+// dependency chain.  (The level schedule keeps plain read-only loads: with
+// its rows per warp step a compile-time constant they measured faster.)
 __device__ __forceinline__ int ld_pinned(const int32_t *p) {
   int v;
   asm volatile("ld.global.nc.s32 %0, [%1];" : "=r"(v) : "l"(p));
@@ -354,8 +355,9 @@ __device__ __forceinline__ void sell_rows(const Sell<TV> &M, const TX *__restric
 //
 // Each slab stores its rows in ELL form (width = the slab's longest row,
 // rounded up to 8), so the address of a row's entries follows from the row
-// index without a dependent load.  A warp takes TRSV_ROWS consecutive rows
-// at a time, 32 / TRSV_ROWS lanes per row, 16 entries of each row in flight,
+// index without a dependent load.  A warp takes R consecutive rows at a time
+// (R = 4, or 2 for factors with wide rows; a compile-time constant of each
+// instance), 32 / R lanes per row, TRSV_EPL entries per lane in flight,
 // and fetches the
 // next group's entries, right-hand sides (from shared memory) and pivots
 // (reciprocals computed on the host, so no division and no load sits on the
@@ -393,27 +395,28 @@ struct TriPre {
   int rnd;
 };
 
-template <bool LOWER, typename T, typename RHS>
+template <bool LOWER, int R, typename T, typename RHS>
 __device__ __forceinline__ void trsv_fetch(const TriEll<T> &M, int64_t b0, int64_t base, int wd, int64_t ngrp,
-                                           int64_t it, int q, int g, int lanes, RHS &rhs_of, TriPre<T> &P) {
+                                           int64_t it, int q, int g, RHS &rhs_of, TriPre<T> &P) {
+  constexpr int lanes = 32 / R;
   const int64_t gi = LOWER ? it : ngrp - 1 - it;
-  const int64_t r = b0 + (int64_t)M.rows * gi + q;
+  const int64_t r = b0 + (int64_t)R * gi + q;
   const int64_t e = base + (r - b0) * wd + g;
 #pragma unroll
   for (int k = 0; k < TRSV_EPL; k++) {
     P.c[k] = -1;
     P.a[k] = T(0);
     if (g + k * lanes < wd) {
-      P.c[k] = ld_pinned(M.col + e + k * lanes);
-      P.a[k] = ld_pinned(M.val + e + k * lanes);
+      P.c[k] = __ldg(M.col + e + k * lanes);
+      P.a[k] = __ldg(M.val + e + k * lanes);
     }
   }
-  P.rnd = ld_pinned(M.round + r);
+  P.rnd = __ldg(M.round + r);
   P.rhs = T(0);
   P.rdg = T(1);
   if (g == 0) {
     P.rhs = rhs_of(r);
-    P.rdg = ld_pinned(M.rdiag + r);
+    P.rdg = __ldg(M.rdiag + r);
   }
 }
 
@@ -472,9 +475,9 @@ __device__ __forceinline__ void trsv_wait(const TriSrc<T> &S, const int *c, T *v
   }
 }
 
-template <bool LOWER, typename T, typename RHS>
-__device__ __forceinline__ void trsv_block(const TriEll<T> &M, T *x, int64_t npad, int64_t bsize, int twarps,
-                                           long long spin_ns, int poll_ns, State *st, T *stage_mem, RHS rhs_of) {
+template <bool LOWER, int R, typename T, typename RHS>
+__device__ __noinline__ void trsv_block_r(const TriEll<T> &M, T *x, int64_t npad, int64_t bsize, int twarps,
+                                          long long spin_ns, int poll_ns, State *st, T *stage_mem, RHS rhs_of) {
   const int64_t b0 = (int64_t)grank() * bsize;
   const int64_t b1 = min(npad, b0 + bsize);
   const int64_t nb = b1 > b0 ? b1 - b0 : 0;
@@ -484,8 +487,7 @@ __device__ __forceinline__ void trsv_block(const TriEll<T> &M, T *x, int64_t npa
   __syncthreads();
   const TriSrc<T> S{x, stage, b0, b1};
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int R = M.rows;                    // 4 or 2; bsize is a multiple of 4
-  const int lanes = 32 / R;                // lanes per row
+  constexpr int lanes = 32 / R;            // lanes per row (R = 4 or 2; bsize is a multiple of 4)
   const int64_t ngrp = nb / R;
   int64_t it = warp;
   if (warp < twarps && it < ngrp) {
@@ -524,6 +526,7 @@ __device__ __forceinline__ void trsv_block(const TriEll<T> &M, T *x, int64_t npa
           trsv_wait<1, T>(S, ce, ve, st, spin_ns, poll_ns);
           if (ce[0] >= 0) acc += __ldg(M.val + e + k) * ve[0];
         }
+#pragma unroll
         for (int o = lanes / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
         if (active && g == 0) {
           const T val = (cur.rhs - acc) * cur.rdg;
@@ -536,20 +539,34 @@ __device__ __forceinline__ void trsv_block(const TriEll<T> &M, T *x, int64_t npa
     // two descriptor sets used in turn: the next group's entries load while
     // this one waits, and no register copy waits for those loads
     TriPre<T> p0, p1;
-    trsv_fetch<LOWER, T>(M, b0, base, wd, ngrp, it, q, g, lanes, rhs_of, p0);
+    trsv_fetch<LOWER, R, T>(M, b0, base, wd, ngrp, it, q, g, rhs_of, p0);
     for (;;) {
       const int64_t it1 = it + twarps;
-      if (it1 < ngrp) trsv_fetch<LOWER, T>(M, b0, base, wd, ngrp, it1, q, g, lanes, rhs_of, p1);
+      if (it1 < ngrp) trsv_fetch<LOWER, R, T>(M, b0, base, wd, ngrp, it1, q, g, rhs_of, p1);
       process(p0, it);
       if (it1 >= ngrp) break;
       const int64_t it2 = it1 + twarps;
-      if (it2 < ngrp) trsv_fetch<LOWER, T>(M, b0, base, wd, ngrp, it2, q, g, lanes, rhs_of, p0);
+      if (it2 < ngrp) trsv_fetch<LOWER, R, T>(M, b0, base, wd, ngrp, it2, q, g, rhs_of, p0);
       process(p1, it1);
       if (it2 >= ngrp) break;
       it = it2;
     }
   }
   __syncthreads();
+}
+
+// The level schedule with the rows per warp step of the factor's layout
+// (4, or 2 for factors with wide rows), each a compile-time instance.  The
+// instances are called, not inlined: inside the persistent solver kernels
+// the inlined solves raised register spills and measured 4-10 % slower per
+// whole solve (the call happens once per triangular solve).
+template <bool LOWER, typename T, typename RHS>
+__device__ __forceinline__ void trsv_block(const TriEll<T> &M, T *x, int64_t npad, int64_t bsize, int twarps,
+                                           long long spin_ns, int poll_ns, State *st, T *stage_mem, RHS rhs_of) {
+  if (M.rows == 2)
+    trsv_block_r<LOWER, 2, T>(M, x, npad, bsize, twarps, spin_ns, poll_ns, st, stage_mem, rhs_of);
+  else
+    trsv_block_r<LOWER, 4, T>(M, x, npad, bsize, twarps, spin_ns, poll_ns, st, stage_mem, rhs_of);
 }
 
 // Chain schedule of the sync-free triangular solve, one slab per CTA.

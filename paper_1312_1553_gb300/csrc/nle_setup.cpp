@@ -187,6 +187,12 @@ int ic_factor_host(int64_t n, const int64_t *rp, const int32_t *ci, const double
       push_bucket(j);
     }
   }
+  factor_from_columns(n, std::move(cs), std::move(rows), std::move(vals), F);
+  return 0;
+}
+
+void factor_from_columns(int64_t n, std::vector<int64_t> cs, std::vector<int32_t> rows, std::vector<double> vals,
+                         Factor &F) {
   // L by rows (diagonal last), from the columns
   const int64_t nnz = (int64_t)rows.size();
   F.n = n;
@@ -226,7 +232,6 @@ int ic_factor_host(int64_t n, const int64_t *rp, const int32_t *ci, const double
     F.nlevL = std::max<int64_t>(F.nlevL, F.levL[i] + 1);
     F.nlevU = std::max<int64_t>(F.nlevU, F.levU[i] + 1);
   }
-  return 0;
 }
 
 // Greedy colouring in natural order: row i takes the smallest colour not

@@ -79,6 +79,10 @@ int validate_csr(int64_t n, int64_t nnz, const int64_t *rp, const int32_t *ci, c
 // non-positive pivot (column in *bad_col).
 int ic_factor_host(int64_t n, const int64_t *rp, const int32_t *ci, const double *va, int lfil, double tau,
                    Factor &F, int64_t *bad_col);
+// The factor from L by columns (column k: entries cs[k]..cs[k+1]-1 of
+// rows/vals, diagonal first, rows ascending): L by rows and the levels.
+void factor_from_columns(int64_t n, std::vector<int64_t> cs, std::vector<int32_t> rows, std::vector<double> vals,
+                         Factor &F);
 
 // Greedy multicolour ordering (nle_multicolor_order in nle.h): perm[new] =
 // old, rows by colour then by row.  Returns the number of colours.

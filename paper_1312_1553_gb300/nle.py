@@ -26,6 +26,7 @@ NLE_FP64, NLE_MIXED = 0, 1
 NLE_ORDER_NATURAL, NLE_ORDER_MULTICOLOR1, NLE_ORDER_MULTICOLOR2 = 0, 1, 2
 NLE_BFGS_SIMPLIFIED, NLE_BFGS_FULL = 0, 1
 NLE_SCHED_AUTO, NLE_SCHED_LEVEL, NLE_SCHED_CHAIN = 0, 1, 2
+NLE_IC_AUTO, NLE_IC_HOST, NLE_IC_DEVICE = 0, 1, 2
 SCHEDULES = {1: "level", 2: "chain"}
 EXITS = ("tol", "maxit", "eigres", "stagnation", "breakdown")
 PHASES = ("spmv", "update", "fwd_solve", "bwd_solve", "dots", "direction", "outer_fp64", "other")
@@ -44,7 +45,8 @@ class nle_options(ctypes.Structure):
                 ("exit_stagnation", ctypes.c_int), ("dacg_recompute", ctypes.c_int),
                 ("spin_timeout_s", ctypes.c_double), ("grid_ctas", ctypes.c_int), ("trsv_warps", ctypes.c_int),
                 ("ordering", ctypes.c_int), ("bfgs_update", ctypes.c_int), ("trsv_schedule", ctypes.c_int),
-                ("trsv_poll_ns", ctypes.c_int), ("trsv_rows", ctypes.c_int)]
+                ("trsv_poll_ns", ctypes.c_int), ("trsv_rows", ctypes.c_int),
+                ("ic_device", ctypes.c_int)]
 
 
 class nle_stats(ctypes.Structure):
@@ -58,7 +60,8 @@ class nle_stats(ctypes.Structure):
                 ("kernel_launches", ctypes.c_int64), ("ms_phase", ctypes.c_double * 8), ("ascending", ctypes.c_int),
                 ("ms_batch", ctypes.c_double), ("trsv_schedule", ctypes.c_int), ("tune_ms_level", ctypes.c_double),
                 ("tune_ms_chain", ctypes.c_double), ("tune_ms_level2", ctypes.c_double), ("strands", ctypes.c_int64),
-                ("trsv_rows", ctypes.c_int)]
+                ("trsv_rows", ctypes.c_int), ("ic_on_device", ctypes.c_int), ("ms_ic_factor", ctypes.c_double),
+                ("ms_ic_kernel", ctypes.c_double), ("ms_ic_setup", ctypes.c_double)]
 
 
 class nle_pcg_info(ctypes.Structure):
@@ -286,7 +289,8 @@ class Eigensolver:
         return lam, V, stats_dict(stats)
 
     def last_stats(self) -> dict:
-        """Statistics of the last solve on this handle (single or batched)."""
+        """Statistics of the last solve on this handle (single or batched); after
+        factor_ic alone, only the set-up fields (schedule, autotuner, IC factor)."""
         st = nle_stats()
         self._check(nle_get_stats(self.h, st))
         return stats_dict(st)
@@ -373,7 +377,9 @@ def stats_dict(s: nle_stats) -> dict:
                 ms_phase=dict(zip(PHASES, [float(x) for x in s.ms_phase])), ascending=bool(s.ascending),
                 ms_batch=float(s.ms_batch), trsv_schedule=SCHEDULES.get(int(s.trsv_schedule), "none"),
                 tune_ms=dict(level=float(s.tune_ms_level), chain=float(s.tune_ms_chain),
-                             level2=float(s.tune_ms_level2)), strands=int(s.strands), trsv_rows=int(s.trsv_rows))
+                             level2=float(s.tune_ms_level2)), strands=int(s.strands), trsv_rows=int(s.trsv_rows),
+                ic=dict(on_device=int(s.ic_on_device), factor_ms=float(s.ms_ic_factor),
+                        kernel_ms=float(s.ms_ic_kernel), setup_ms=float(s.ms_ic_setup)))
 
 
 def _eigsh_function():

@@ -44,6 +44,7 @@ def test_default_options(lib):
     assert o.k_max == 5 and o.tau_pcg == 1e-2 and o.tau_dacg == 1e-2 and o.max_dacg == 5000
     assert o.precision == nle.NLE_FP64 and o.exit_eigres == 1 and o.exit_stagnation == 1
     assert o.trsv_schedule == nle.NLE_SCHED_AUTO and o.trsv_warps == 16 and o.trsv_rows == 0 and o.trsv_poll_ns == 0
+    assert o.ic_device == nle.NLE_IC_AUTO
 
 
 def _create(A, opt=None):
@@ -71,6 +72,10 @@ def test_argument_errors_without_device(lib):
     o.trsv_schedule = 7
     st, h, msg = _create(A, o)
     assert st == 1 and "trsv_schedule" in msg
+    o = nle.nle_default_options()
+    o.ic_device = 3
+    st, h, msg = _create(A, o)
+    assert st == 1 and "ic_device" in msg
 
 
 @pytest.mark.parametrize("case", ["unsorted", "asym", "nodiag", "negdiag"])
