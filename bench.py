@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 arm (profiling runs)")
     ap.add_argument("--skip-e2e", action="store_true", help="profiling runs: skip the host-buffer pass")
+    ap.add_argument("--no-ic-host", action="store_true", help="skip the host IC factor timed for comparison")
     ap.add_argument("--pairs", type=int, default=0, help="profiling runs: solve only the first P eigenpairs")
     ap.add_argument("--trsv-warps", type=int, default=0, help="0 = library default")
     ap.add_argument("--ordering", default="natural", choices=["natural", "mc1", "mc2"],
@@ -351,6 +352,9 @@ def batch_main(args, world, rank, local, cpu):
             s.factor_ic(30, 1e-2)
             solvers.append(s)
         ic_seconds = time.perf_counter() - t0
+        ics = [s.last_stats()["ic"] for s in solvers]
+        ic_info = dict(on_device=sum(i["on_device"] for i in ics), problems=len(ics),
+                       factor_ms=sum(i["factor_ms"] for i in ics), kernel_ms=sum(i["kernel_ms"] for i in ics))
         nnz_l = [int(s.get_factor()["Lrowptr"][-1]) for s in solvers]
         X0h = [torch.tensor(batch_problem_start(A, b), dtype=torch.float64).pin_memory() for b, A in enumerate(mats)]
         X0d = [x.to("cuda") for x in X0h]
@@ -421,7 +425,7 @@ def batch_main(args, world, rank, local, cpu):
                 config=dict(workload=f"{BATCH}: {count} random geometric graph Laplacians + 1e-3 I, "
                                      f"n ~ U[2000, 60000], p = {BATCH_P}",
                             n_total=sum(A.n for A in mats), nnz_total=sum(A.nnz for A in mats), lfil=30, tau_ic=1e-2,
-                            tol=1e-8, ic_seconds=ic_seconds, l2="working set > 129 MB L2 (no flush needed)",
+                            tol=1e-8, ic_seconds=ic_seconds, ic_factor=ic_info, l2="working set > 129 MB L2 (no flush needed)",
                             parallelism=f"replicas{world}" if world > 1 else
                             f"single GPU, groups of {args.batch_ctas or (4 if prec == nle.NLE_MIXED else 8)} CTAs"),
                 roofline=dict(bound="hbm", achieved=achieved, peak=peak, unit="GB/s", frac=achieved / peak,
@@ -511,6 +515,16 @@ def main():
         t0 = time.perf_counter()
         s.factor_ic(st["lfil"], st["tau_ic"])
         ic_seconds = time.perf_counter() - t0
+        ic_stats = s.last_stats()["ic"]
+        ic_info = dict(where="device" if ic_stats["on_device"] else "host", factor_ms=ic_stats["factor_ms"],
+                       kernel_ms=ic_stats["kernel_ms"], setup_ms=ic_stats["setup_ms"])
+        if ic_stats["on_device"] and not args.no_ic_host and rank == 0:
+            # the same factor computed on the host, for comparison (set-up only)
+            sh = nle.Eigensolver(A, dict(opts, ic_device=nle.NLE_IC_HOST, trsv_schedule=nle.NLE_SCHED_LEVEL),
+                                 stream=stream)
+            sh.factor_ic(st["lfil"], st["tau_ic"])
+            ic_info["host_factor_ms"] = sh.last_stats()["ic"]["factor_ms"]
+            sh.close()
         F = s.get_factor()
         nnz_l = int(F["Lrowptr"][-1])
         x0 = torch.tensor(X0, dtype=torch.float64, device="cuda")
@@ -647,6 +661,7 @@ def main():
                             n=A.n, nnz=A.nnz, p=p, lfil=st["lfil"], tau_ic=st["tau_ic"], tol=st["tol"],
                             precision="FP32 bulk + FP64 outer step" if prec == nle.NLE_MIXED else "FP64",
                             nnz_L=nnz_l, nlev_L=F["nlevL"], ordering=args.ordering, bfgs=args.bfgs, ic_seconds=ic_seconds,
+                            ic_factor=ic_info,
                             trsv_schedule=all_stats[-1]["trsv_schedule"], schedule_request=args.schedule,
                             tune_ms=all_stats[-1]["tune_ms"], strands=all_stats[-1]["strands"],
                             l2="working set > 129 MB L2 (no flush needed)",

@@ -139,8 +139,10 @@ def test_batch_bounded_wait_reports_timeout_and_context_survives(nle):
     X0s = [W.start_vectors(A.n, p, 760 + i) for i, A in enumerate(mats)]
     bad = []
     for A in mats:
+        # factor on the host (the device factor's own bounded wait is tested
+        # in test_gpu_ict.py)
         s = nle.Eigensolver(A, dict(precision=nle.NLE_MIXED, grid_ctas=4, spin_timeout_s=1e-9,
-                                    trsv_schedule=nle.NLE_SCHED_LEVEL))
+                                    trsv_schedule=nle.NLE_SCHED_LEVEL, ic_device=nle.NLE_IC_HOST))
         s.factor_ic(30, 1e-2)
         bad.append(s)
     with pytest.raises(nle.NLEError) as e:

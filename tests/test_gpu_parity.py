@@ -505,7 +505,9 @@ def test_bounded_wait_reports_timeout_and_context_survives(nle):
     NLE_ERR_TIMEOUT; the kernels return on their own and the same process
     then solves normally."""
     A, st = load("diff3d7_24")
-    s = solver(nle, A, "mixed", spin_timeout_s=1e-9)
+    # the factor on the host: the device factor's own bounded wait is
+    # tested in test_gpu_ict.py; here the solver's waits run out
+    s = solver(nle, A, "mixed", spin_timeout_s=1e-9, ic_device=nle.NLE_IC_HOST)
     s.factor_ic(st["lfil"], st["tau_ic"])
     with pytest.raises(nle.NLEError) as e:
         s.solve(2, 1e-8, 100, 20, W.start_vectors(A.n, 2, 1))
