@@ -379,7 +379,8 @@ nle_status nle_multicolor_order(int64_t n, const int64_t *rowptr, const int32_t 
  *     message in nle_last_error(NULL) and touches no memory;
  *   - the first call on a device looks up the array's device address once
  *     for that device (cudaGetSymbolAddress, with that device current);
- *     make that first call before any stream capture begins;
+ *   - it cannot be called while its stream is being captured into a CUDA
+ *     graph: it reads its error word back and waits for the stream;
  *   - all calls share the array and it keeps the last call's contents (the
  *     call resets what must start fresh), so calls that overlap on the GPU,
  *     on any streams or threads, race: serialise them;

@@ -281,12 +281,12 @@ static Dev<T> make_dev(nle_t h) {
   D.Lw = h->L_w.as<int32_t>();
   D.Lcol = h->L_col.as<int32_t>();
   D.Lval = h->L_val.as<T>();
-  D.Lround = h->L_round.as<uint8_t>();
+  D.Lround = h->L_round.as<uint16_t>();
   D.Uoff = h->U_off.as<int64_t>();
   D.Uw = h->U_w.as<int32_t>();
   D.Ucol = h->U_col.as<int32_t>();
   D.Uval = h->U_val.as<T>();
-  D.Uround = h->U_round.as<uint8_t>();
+  D.Uround = h->U_round.as<uint16_t>();
   D.rdiag = h->d_diag.as<T>();
   D.chain = h->chain;
   D.trows = h->trows;

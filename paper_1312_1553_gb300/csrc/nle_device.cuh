@@ -92,11 +92,6 @@ __device__ __forceinline__ double ld_pinned(const double *p) {
   asm volatile("ld.global.nc.f64 %0, [%1];" : "=d"(v) : "l"(p));
   return v;
 }
-__device__ __forceinline__ int ld_pinned(const uint8_t *p) {
-  unsigned short v;
-  asm volatile("ld.global.nc.u8 %0, [%1];" : "=h"(v) : "l"(p));
-  return (int)v;
-}
 
 // ---------------------------------------------------------------------------
 // memory-model helpers (PTX): relaxed gpu-scope loads/stores bypass L1 and
@@ -382,8 +377,8 @@ struct TriEll {
   const int32_t *col;    // -1 = padding
   const T *val;
   const T *rdiag;         // npad: reciprocal pivots 1 / L_rr
-  const uint8_t *round;   // npad: round of the row inside its group of rows (low nibble) and
-                          // the group's last round (high nibble)
+  const uint16_t *round;  // npad: round of the row inside its group of rows (bits 0-3), the
+                          // group's last round (4-7) and overflow steps (8-15, 255: to width)
   int rows;               // rows a warp takes at a time: 4 (8 lanes per row) or 2 (16 lanes)
 };
 
@@ -499,7 +494,9 @@ __device__ __noinline__ void trsv_block_r(const TriEll<T> &M, T *x, int64_t npad
     auto process = [&](const TriPre<T> &cur, int64_t itc) {
       const int64_t gi = LOWER ? itc : ngrp - 1 - itc;
       const int64_t r = b0 + (int64_t)R * gi + q;
-      const int rounds = 1 + (cur.rnd >> 4);  // the same in every lane of the group
+      const int rounds = 1 + ((cur.rnd >> 4) & 15);  // the same in every lane of the group
+      const int steps = cur.rnd >> 8;                 // overflow steps, likewise
+      const int kend = steps == 255 ? wd : min(wd, TRSV_EPL * lanes + steps * lanes);
       for (int rd = 0; rd < rounds; rd++) {
         const bool active = ((cur.rnd & 15) == rd);
         int c[TRSV_EPL];
@@ -516,11 +513,12 @@ __device__ __noinline__ void trsv_block_r(const TriEll<T> &M, T *x, int64_t npad
         for (int k = 0; k < TRSV_EPL; k++)
           if (c[k] >= 0) acc += cur.a[k] * v[k];
         // entries beyond the first TRSV_EPL * lanes of a row, one per lane
-        // and step; every lane takes the same number of steps
+        // and step, up to the group's longest row (not the slab's width);
+        // every lane takes the same number of steps
         const int64_t e = base + (r - b0) * wd;
-        for (int k0 = TRSV_EPL * lanes; k0 < wd; k0 += lanes) {
+        for (int k0 = TRSV_EPL * lanes; k0 < kend; k0 += lanes) {
           const int k = k0 + g;
-          int ce[1] = {(active && k < wd) ? __ldg(M.col + e + k) : -1};
+          int ce[1] = {(active && k < kend) ? __ldg(M.col + e + k) : -1};
           T ve[1] = {T(0)};
           if (ce[0] >= 0) ve[0] = trsv_peek(S, ce[0]);
           trsv_wait<1, T>(S, ce, ve, st, spin_ns, poll_ns);

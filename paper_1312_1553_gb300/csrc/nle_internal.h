@@ -121,7 +121,7 @@ struct Dev {
   const int32_t *Lw = nullptr, *Uw = nullptr, *Lcol = nullptr, *Ucol = nullptr;
   const T *Lval = nullptr, *Uval = nullptr;
   const T *rdiag = nullptr;  // reciprocal diagonal of L (1 on padding rows)
-  const uint8_t *Lround = nullptr, *Uround = nullptr;
+  const uint16_t *Lround = nullptr, *Uround = nullptr;
   int trows = TRSV_ROWS;  // level schedule: rows a warp takes at a time (4, or 2 for wide rows)
   // chain schedule (chain = 1): the device order is the factored matrix's
   // own row order, and each slab's rows are solved as per-warp task lists

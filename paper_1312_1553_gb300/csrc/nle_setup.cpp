@@ -388,24 +388,34 @@ static void ell(int64_t n, int64_t npad, int64_t bsize, bool lower, const std::v
             if ((*lev)[u] == (*lev)[t]) below = false;  // count each level once
           rank += below;
         }
-        out.round[r] = (uint8_t)rank;
+        out.round[r] = (uint16_t)rank;
       }
     } else if (lower) {
       for (int64_t r = g0; r < g1; r++)
         for (int64_t e = rp[r]; e < rp[r + 1]; e++)
-          if (col[e] >= g0) out.round[r] = std::max<uint8_t>(out.round[r], out.round[col[e]] + 1);
+          if (col[e] >= g0) out.round[r] = std::max<uint16_t>(out.round[r], out.round[col[e]] + 1);
     } else {
       for (int64_t r = g1 - 1; r >= g0; r--)
         for (int64_t e = rp[r]; e < rp[r + 1]; e++)
-          if (col[e] < g1) out.round[r] = std::max<uint8_t>(out.round[r], out.round[col[e]] + 1);
+          if (col[e] < g1) out.round[r] = std::max<uint16_t>(out.round[r], out.round[col[e]] + 1);
     }
     // every row also carries the number of rounds of its group, less one,
     // in the high nibble (rounds <= R <= 4), so a warp needs no reduction
     // to learn it
     // (padding rows past n included: every lane of the group must agree)
-    uint8_t last = 0;
-    for (int64_t r = g0; r < g1; r++) last = std::max(last, out.round[r]);
-    for (int64_t r = g0; r < std::min(npad, g0 + R); r++) out.round[r] = (uint8_t)(out.round[r] | (last << 4));
+    // and the group's overflow steps in the high byte: the entries of its
+    // longest row past the TRSV_EPL * 32 / R prefetched ones, in steps of 32 / R,
+    // so that the solve stops at the group's last entry, not the slab's width
+    uint16_t last = 0;
+    int64_t glen = 0;
+    for (int64_t r = g0; r < g1; r++) {
+      last = std::max(last, out.round[r]);
+      glen = std::max<int64_t>(glen, rp[r + 1] - rp[r]);
+    }
+    const int64_t lanes = 32 / R, pre = TRSV_EPL * lanes;
+    const int64_t steps = std::min<int64_t>(255, glen > pre ? (glen - pre + lanes - 1) / lanes : 0);
+    for (int64_t r = g0; r < std::min(npad, g0 + R); r++)
+      out.round[r] = (uint16_t)(out.round[r] | (last << 4) | (steps << 8));
   }
 }
 

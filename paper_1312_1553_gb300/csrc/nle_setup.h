@@ -45,7 +45,11 @@ struct EllHost {
   std::vector<int32_t> width;  // per slab: entries per row, multiple of 8
   std::vector<int32_t> col;    // -1 = padding
   std::vector<TV> val;
-  std::vector<uint8_t> round;  // per row: its round inside its group of TRSV_ROWS rows
+  // per row (level schedule): bits 0-3 its round inside its group of R
+  // rows, bits 4-7 the group's last round, bits 8-15 the group's overflow
+  // steps (entries past the 2 * 32 / R a warp step prefetches, in steps of
+  // 32 / R; 255: up to the slab's width)
+  std::vector<uint16_t> round;
 };
 
 // Chain schedule of one strictly triangular factor (see trsv_chain): the

@@ -70,14 +70,14 @@ extern "C" int64_t shim_level(int lower, int64_t bsize, int R, int64_t *nent, in
   return npad;
 }
 
-extern "C" void shim_level_get(int lower, int64_t *off, int32_t *width, int32_t *col, double *val, uint8_t *round,
+extern "C" void shim_level_get(int lower, int64_t *off, int32_t *width, int32_t *col, double *val, uint16_t *round,
                                double *rdiag, int32_t *perm) {
   const EllHost<double> &E = lower ? g_S.L : g_S.U;
   memcpy(off, E.off.data(), E.off.size() * 8);
   memcpy(width, E.width.data(), E.width.size() * 4);
   memcpy(col, E.col.data(), E.col.size() * 4);
   memcpy(val, E.val.data(), E.val.size() * 8);
-  memcpy(round, E.round.data(), E.round.size());
+  memcpy(round, E.round.data(), E.round.size() * 2);
   memcpy(rdiag, g_S.diag.data(), g_S.diag.size() * 8);
   memcpy(perm, g_perm.data(), g_perm.size() * 4);
 }

@@ -194,7 +194,7 @@ def level_layout(lib, A, lfil, tau, bsize, R, lower):
     npad = lib.shim_level(1 if lower else 0, bsize, R, ctypes.byref(nent), ctypes.byref(nslab))
     ns = nslab.value
     E = dict(off=np.zeros(ns + 1, np.int64), width=np.zeros(ns, np.int32), col=np.zeros(nent.value, np.int32),
-             val=np.zeros(nent.value), round=np.zeros(npad, np.uint8), rdiag=np.zeros(npad),
+             val=np.zeros(nent.value), round=np.zeros(npad, np.uint16), rdiag=np.zeros(npad),
              perm=np.zeros(A.n, np.int32), ns=ns, npad=npad)
     lib.shim_level_get(1 if lower else 0, E["off"].ctypes.data, E["width"].ctypes.data, E["col"].ctypes.data,
                        E["val"].ctypes.data, E["round"].ctypes.data, E["rdiag"].ctypes.data, E["perm"].ctypes.data)
@@ -206,7 +206,10 @@ def simulate_level(E, n, bsize, R, rhs_dev, lower, nwarps=NWARP):
     positions, taken from the front for L and from the back for U) belongs
     to warp gi mod nwarps, which takes its groups in order; the rows of a
     group run in rounds (round[r]), a round when all its rows' entries are
-    computed."""
+    computed.  A row's entries are read as the kernel reads them: the
+    2 * 32 / R prefetched ones, then the group's overflow steps of 32 / R
+    (high byte of round[r]; 255: up to the slab's width); every entry past
+    that must be padding."""
     npad = E["npad"]
     x = np.full(npad, np.nan)
     done = np.zeros(npad, bool)
@@ -228,14 +231,19 @@ def simulate_level(E, n, bsize, R, rhs_dev, lower, nwarps=NWARP):
                 gi = it if lower else qd["ngrp"] - 1 - it
                 rows = [qd["b0"] + R * gi + q for q in range(R)]
                 s = qd["s"]
-                wd = E["width"][s]
+                steps = int(E["round"][rows[0]]) >> 8
+                assert all(int(E["round"][r]) >> 8 == steps for r in rows)
+                wd = int(E["width"][s]) if steps == 255 else min(int(E["width"][s]), (2 + steps) * (32 // R))
+                for r in rows:
+                    e = E["off"][s] + (r - qd["b0"]) * int(E["width"][s])
+                    assert np.all(E["col"][e + wd:e + int(E["width"][s])] == -1), "a real entry past the group's length"
                 rounds = 1 + max(int(E["round"][r]) & 15 for r in rows)
-                assert all(1 + (int(E["round"][r]) >> 4) == rounds for r in rows)
+                assert all(1 + ((int(E["round"][r]) >> 4) & 15) == rounds for r in rows)
                 rd = qd["rnd"]
                 act = [r for r in rows if (int(E["round"][r]) & 15) == rd]
                 ready = True
                 for r in act:
-                    e = E["off"][s] + (r - qd["b0"]) * wd
+                    e = E["off"][s] + (r - qd["b0"]) * int(E["width"][s])
                     for k in range(wd):
                         c = E["col"][e + k]
                         if c >= 0 and not done[c]:
@@ -243,7 +251,7 @@ def simulate_level(E, n, bsize, R, rhs_dev, lower, nwarps=NWARP):
                 if not ready:
                     break
                 for r in act:
-                    e = E["off"][s] + (r - qd["b0"]) * wd
+                    e = E["off"][s] + (r - qd["b0"]) * int(E["width"][s])
                     acc = 0.0
                     for k in range(wd):
                         c = E["col"][e + k]
