@@ -269,7 +269,10 @@ __global__ void __launch_bounds__(32 * ICT_WARPS, 1)
             v = ld_rlx(cval + base + lane);
           }
           c = __shfl_sync(0xffffffffu, c, 0);
-          const bool ok = lane >= c || (r >= 0 && v == v);
+          // a written slot: not the all-ones fill (tested on the bits: a
+          // floating-point test in this spin would occupy the FP64 pipe the
+          // finishing columns need)
+          const bool ok = lane >= c || (r >= 0 && __double_as_longlong(v) != -1LL);
           if (c >= 1 && __all_sync(0xffffffffu, ok)) break;
           if (wait_expired(++polls, 16, t0, spin_ns, err, j, lane)) return;
         }
